@@ -1,0 +1,126 @@
+"""Pins of the oracle's multigrid against direct solves, convergence order and invariants."""
+
+import numpy as np
+import pytest
+
+from oracle import direct, fem, mg
+from synth import node_coords, standard_normal
+
+
+def _rhs(g, seed):
+    b = fem.lumped_mass(g.shape, g.h) * standard_normal(seed, int(np.prod(g.shape))).reshape(g.shape)
+    b[mg.dirichlet_mask(g)] = 0.0
+    if mg.is_singular(g):
+        b -= b.mean()
+    return b
+
+
+def test_coarsening_schedule():
+    sizes = lambda n: [G.n for G in mg.hierarchy(mg.Grid(n, (1.0, 1.0, 1.0)))]
+    assert sizes((33,) * 3) == [(33,) * 3, (17,) * 3, (9,) * 3, (5,) * 3, (3,) * 3]
+    assert len(sizes((257,) * 3)) == 8
+    assert sizes((97,) * 3)[-1] == (4, 4, 4)
+    assert sizes((129, 65, 65))[-1] == (5, 3, 3)
+
+
+def test_prolongation_exact_for_trilinear_fields():
+    """P reproduces any trilinear function exactly (it is Q1 interpolation)."""
+    gf = mg.Grid((9, 5, 17), (0.1, 0.2, 0.05))
+    gc = gf.coarse()
+    xf, yf, zf = node_coords(gf.n, gf.h)
+    xc, yc, zc = node_coords(gc.n, gc.h)
+    f = lambda x, y, z: 1 + 2 * x - y + 3 * z + x * y - 2 * y * z + x * y * z
+    np.testing.assert_allclose(mg.prolong_raw(gc, f(xc, yc, zc)), f(xf, yf, zf), atol=1e-14)
+
+
+@pytest.mark.parametrize("n,bc", [
+    (5, (True,) * 6),
+    (9, (True,) * 6),
+    (9, (False,) * 5 + (True,)),
+    (9, (False,) * 6),
+    (5, (False,) * 6),
+])
+def test_vcycle_converges_to_dense_solution(n, bc):
+    """V-cycles iterated to 1e-14 agree with dense LU to 1e-12 (zero mean when singular)."""
+    g = mg.Grid((n, n, n), (1.0 / (n - 1),) * 3, bc)
+    b = _rhs(g, 7)
+    x, hist = mg.pressure_solve(g, b, rtol=1e-14, max_cycles=300)
+    assert hist[-1] <= 1e-14
+    xd = direct.solve_dense(g, b)
+    if mg.is_singular(g):
+        x = x - x.mean()
+        xd = xd - xd.mean()
+    assert np.linalg.norm(x - xd) <= 1e-12 * np.linalg.norm(xd)
+
+
+def test_vcycle_variable_coefficient_matches_dense():
+    g = mg.Grid((9, 9, 9), (0.125,) * 3, (False,) * 5 + (True,))
+    k = 1.0 / (1.0 + 9.0 * (standard_normal(5, 729).reshape(g.shape) > 0.5))
+    b = _rhs(g, 11)
+    x, hist = mg.pressure_solve(g, b, k=k, rtol=1e-14, max_cycles=500)
+    xd = direct.solve_dense(g, b, k)
+    assert np.linalg.norm(x - xd) <= 1e-12 * np.linalg.norm(xd)
+
+
+def test_cg_matches_dense():
+    g = mg.Grid((9, 5, 9), (0.125, 0.25, 0.125), (True,) * 6)
+    b = _rhs(g, 2)
+    np.testing.assert_allclose(direct.solve_cg(g, b), direct.solve_dense(g, b), atol=1e-13)
+
+
+def test_manufactured_solution_second_order():
+    """p = sin(pi x) sin(pi y) sin(pi z), f = 3 pi^2 p: nodal max error is O(h^2)."""
+    errs = []
+    ns = [9, 17, 33]
+    for n in ns:
+        h = 1.0 / (n - 1)
+        g = mg.Grid((n, n, n), (h, h, h), (True,) * 6)
+        x, y, z = node_coords(g.n, g.h)
+        p = np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z)
+        b = fem.lumped_mass(g.shape, g.h) * 3 * np.pi**2 * p
+        b[mg.dirichlet_mask(g)] = 0.0
+        sol, _ = mg.pressure_solve(g, b, rtol=1e-13, max_cycles=200)
+        errs.append(np.abs(sol - p).max())
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(1.9 <= o <= 2.1 for o in orders), orders
+
+
+def test_constant_field_zero_residual_and_hydrostatic_line():
+    """A.1 = 0 on natural rows; a linear field is reproduced exactly by the solve."""
+    g = mg.Grid((9, 9, 9), (0.125,) * 3, (False,) * 5 + (True,))
+    r = mg.residual(g, np.zeros(g.shape), np.ones(g.shape))
+    assert np.abs(r).max() < 1e-14
+    # linear p = 1 - z with zero source: the natural boundary flux of the linear field is the
+    # only right-hand side; b = A p; the solve from zero with p fixed at the Dirichlet top
+    _, _, z = node_coords(g.n, g.h)
+    p = 1.0 - z
+    b = mg.stencil_apply(g, p)
+    b[mg.dirichlet_mask(g)] = 0.0
+    sol, _ = mg.pressure_solve(g, b, rtol=1e-14, max_cycles=300)
+    assert np.abs(sol - p).max() < 1e-12
+
+
+def test_jacobi_symbol_values():
+    """Weighted Jacobi on Fourier modes, from the symbols of K1 = [-1,2,-1]/h, M1 = h[1,4,1]/6.
+
+    D^-1 A has symbol 3/2 on the face mode (pi,0,0), 1 on (pi,pi,0) and 1/2 on the checkerboard
+    (pi,pi,pi); with omega = 2/3 one sweep multiplies them by 0, 1/3 and 2/3 at nodes that do not
+    see the boundary.  (2/3 is the smoothing factor of the cycle.)
+    """
+    n = 17
+    g = mg.Grid((n, n, n), (1 / 16,) * 3, (True,) * 6)
+    iz, iy, ix = np.indices(g.shape)
+    for mode, factor in (((ix,), 0.0), ((ix, iy), 1 / 3), ((ix, iy, iz), 2 / 3)):
+        e = (-1.0) ** sum(mode)
+        e = np.where(mg.dirichlet_mask(g), 0.0, e)
+        e1 = mg.jacobi(g, np.zeros(g.shape), e)
+        inner = (slice(2, -2),) * 3
+        np.testing.assert_allclose(e1[inner], factor * e[inner], atol=1e-13)
+
+
+def test_pressure_solve_history_monotone():
+    n = 17
+    g = mg.Grid((n, n, n), (1 / 16,) * 3, (True,) * 6)
+    b = _rhs(g, 0)
+    _, hist = mg.pressure_solve(g, b, fixed_cycles=10)
+    assert len(hist) == 11 and all(hist[i + 1] < hist[i] for i in range(10))
