@@ -1,0 +1,180 @@
+/*
+ * nn4.h - C ABI of the GB300 pressure-multigrid library (Q1 finite elements on vertex grids).
+ *
+ * The library implements the pressure-correction multigrid of Chen, Heaney, Gomes, Matar and
+ * Pain, "Solving the discretised multiphase flow equations with interface capturing on
+ * structured grids using machine learning libraries" (arXiv 2401.06755), Section 2.4, together
+ * with the explicit Petrov-Galerkin volume-fraction and momentum residuals that feed it
+ * (Sections 2.3.1, 2.3.2, 2.3.4 and 2.3.5).  All compute runs in CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call
+ *   - A field on a grid with n = (nx, ny, nz) nodes is a device array with x fastest, then y,
+ *     then z.  Element (i, j, k) lives at offset i + pitch * (j + ny * k); `pitch` is given in
+ *     elements by the nn4_grid passed with the array, must be >= nx, and pitch * sizeof(elem)
+ *     must be a multiple of 16 bytes.  nn4_row_pitch() returns the pitch the library uses for
+ *     its own arrays (a multiple of 128 bytes).  Padding elements are never read or written.
+ *   - Node i of an axis sits at i * h; the grid covers the closed box [0, (n-1) h].
+ *   - Each of the six faces (x-, x+, y-, y+, z-, z+) is Dirichlet (nodes on it are stored
+ *     values that never change; their residual and correction are zero) or natural (the
+ *     zero-derivative condition of Section 2.3.3, realised by finite-element truncation).
+ *   - A is the weak form of -laplacian assembled from Q1 elements (the paper's w_lap filter,
+ *     Section 2.2.4, with a positive diagonal).  With a coefficient field k it is Eq. k-T:
+ *     A_k x = 1/2 [ L(k x) + k L x - x L k ].
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as void*, NULL for the
+ *     legacy default stream) unless stated otherwise.  Argument errors are detected on the host
+ *     before anything is launched.  Pointers are never freed by the library.
+ *   - Every function returns an nn4_status; nn4_last_error() gives a message for the calling
+ *     thread.  Device-side failures of bounded waits are latched in a device word that
+ *     nn4_device_error() reads and clears.
+ */
+#ifndef NN4_H
+#define NN4_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NN4_OK = 0,
+  NN4_EINVAL = -1,        /* bad argument (sizes, pointers, alignment, dtype) */
+  NN4_ECUDA = -2,         /* a CUDA runtime or driver call failed */
+  NN4_ENOMEM = -3,        /* device allocation failed (plan creation only) */
+  NN4_ENOCONV = -4,       /* iteration cap reached before the tolerance */
+  NN4_ENONFINITE = -5,    /* a residual norm was NaN or infinite */
+  NN4_ETIMEOUT = -6,      /* a bounded device-side wait gave up */
+  NN4_EBOUNDS = -7,       /* a checked index was out of range (bounds-check builds) */
+  NN4_EUNSUPPORTED = -8   /* valid but unsupported request (e.g. coarsest level too large) */
+} nn4_status;
+
+typedef enum { NN4_F64 = 0, NN4_F32 = 1, NN4_BF16 = 2 } nn4_dtype;
+
+typedef enum { NN4_BC_DIRICHLET = 0, NN4_BC_NATURAL = 1 } nn4_bc;
+
+/* Vertex grid: n nodes per axis, spacing h, one nn4_bc per face (x-, x+, y-, y+, z-, z+),
+ * and the row pitch (in elements) of the arrays passed together with this descriptor. */
+typedef struct {
+  int32_t n[3];
+  double h[3];
+  int32_t bc[6];
+  int64_t pitch;
+} nn4_grid;
+
+/* Row pitch in elements for nx values of dtype dt: nx rounded up to a multiple of 128 bytes.
+ * Returns -1 for a bad argument. */
+int64_t nn4_row_pitch(int32_t nx, nn4_dtype dt);
+
+/* ----------------------------------------------------------------- single multigrid steps */
+
+/* y = A x at every node (Dirichlet nodes included: the assembled row with natural truncation).
+ * Section 2.2.2 (filter application), Section 2.2.4 (w_lap), Eq. k-T when k != NULL.
+ * x, k, y: device arrays of dtype dt on grid g (k may be NULL).  y must not alias x or k.
+ * Errors: NN4_EINVAL for a null x/y, a grid with fewer than 2 nodes on an axis, or a bad pitch. */
+int nn4_stencil_apply(const nn4_grid* g, nn4_dtype dt, const void* x, const void* k, void* y,
+                      void* stream);
+
+/* r = b - A x at free nodes and r = 0 at Dirichlet nodes (the pressure residual of Eq. ph_disc
+ * and Eq. ph_disc2 with the sign convention of A above).  If norm2 != NULL it is a device
+ * double that is overwritten with sum r^2 (accumulated in FP64).  r must not alias b, x or k. */
+int nn4_residual(const nn4_grid* g, nn4_dtype dt, const void* b, const void* x, const void* k,
+                 void* r, double* norm2, void* stream);
+
+/* r_coarse = R r_fine with R = P^T (weights prod_d (1/2)^|offset_d|, stride 2), and
+ * r_coarse = 0 at coarse Dirichlet nodes.  The coarse grid has (n+1)/2 nodes per axis (every
+ * n must be odd and >= 3) and its array uses pitch nn4_row_pitch((nx+1)/2, dt).  Section 2.4
+ * (the sawtooth multigrid: stride-2 restriction). */
+int nn4_restrict(const nn4_grid* fine, nn4_dtype dt, const void* r_fine, void* r_coarse,
+                 void* stream);
+
+/* e_fine = P e_coarse (accumulate = 0) or e_fine += P e_coarse (accumulate != 0), P the
+ * trilinear interpolation (injection at even nodes, averages of 2, 4 or 8 coarse nodes
+ * elsewhere); fine Dirichlet nodes are set to 0 (accumulate = 0) or left unchanged.  Coarse
+ * array pitch as for nn4_restrict.  Section 2.4 (prolongation in the U-Net decoder). */
+int nn4_prolong(const nn4_grid* fine, nn4_dtype dt, const void* e_coarse, void* e_fine,
+                int accumulate, void* stream);
+
+/* One weighted-Jacobi sweep x_out = x_in + omega D^-1 (b - A x_in) at free nodes; Dirichlet
+ * nodes are copied.  D is the exact diagonal of A (boundary rows included).  Section 1.1
+ * ("multigrid with Jacobi smoothing").  x_out must not alias x_in. */
+int nn4_jacobi_smooth(const nn4_grid* g, nn4_dtype dt, const void* b, const void* k,
+                      const void* x_in, void* x_out, double omega, void* stream);
+
+/* ----------------------------------------------------------------- plans and solves */
+
+typedef enum {
+  NN4_OUTER_CYCLES = 0,  /* x += (inner_cycles V-cycles on A e = b - A x): the paper's repeated
+                            cycles, in defect-correction form */
+  NN4_OUTER_FCG = 1      /* flexible CG with the V-cycles as preconditioner (not in the paper;
+                            needed for large density ratios) */
+} nn4_outer;
+
+typedef struct {
+  nn4_dtype inner;       /* storage type of the multigrid hierarchy: F64 = the plain method;
+                            F32 / BF16 = mixed precision (FP32 arithmetic, FP64 outer loop) */
+  int32_t inner_cycles;  /* V-cycles per outer iteration, >= 1 */
+  int32_t outer;         /* nn4_outer */
+  double omega;          /* Jacobi weight, 2/3 in the paper's setting */
+  int32_t use_graph;     /* capture each outer iteration as a CUDA graph (1) or launch eagerly */
+  int32_t check_every;   /* read the residual norm back every this many outer iterations (>=1) */
+} nn4_plan_opts;
+
+/* Fills o with the defaults: F64, 1 cycle, NN4_OUTER_CYCLES, omega 2/3, graphs on, check 1. */
+void nn4_plan_opts_default(nn4_plan_opts* o);
+
+typedef struct nn4_plan_s* nn4_plan;
+
+/* Builds the multigrid hierarchy of grid g (g->pitch is the pitch of the FP64 arrays b, x
+ * and k used with this plan).  k: device FP64 coefficient field on g, or NULL for the constant
+ * coefficient.  Coarsening halves every axis ((n+1)/2) while all axes are odd and >= 5; the
+ * coarsest level is solved with a dense inverse computed here (pseudo-inverse when no face is
+ * Dirichlet).  With k, coarse operators are Galerkin products P^T A P formed on the device.
+ * The plan owns every workspace array; this is the only call that allocates.
+ * Errors: NN4_EINVAL, NN4_ENOMEM, NN4_EUNSUPPORTED (coarsest level above 1024 free nodes). */
+int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* o, nn4_plan* out);
+
+int nn4_plan_destroy(nn4_plan p);
+
+/* One sawtooth V(0,1) cycle on A x = b, in place on x (Section 2.4): residual on the finest
+ * level, restriction down to the coarsest level, exact coarsest solve, then on every level on
+ * the way up prolongation followed by one Jacobi sweep.  b and x are device arrays of the
+ * plan's inner dtype on the fine grid with pitch nn4_row_pitch(nx, inner). */
+int nn4_vcycle(nn4_plan p, const void* b, void* x, void* stream);
+
+typedef struct {
+  int32_t iterations;    /* outer iterations done */
+  int32_t cycles;        /* V-cycles done */
+  double rel_res;        /* final ||b - A x|| / ||b|| (free nodes), recomputed in FP64 */
+  double* history;       /* caller-owned host array or NULL: relative residual after each
+                            outer iteration, history[0] for the initial x */
+  int32_t history_len;   /* capacity of history */
+} nn4_solve_info;
+
+/* Solves A x = b (FP64 device arrays on the plan's grid, pitch g->pitch) from the x given,
+ * until ||b - A x||_2 / ||b||_2 <= rtol or max_iters outer iterations.  Synchronises the stream.
+ * Returns NN4_ENOCONV (with info filled) when the cap is reached, NN4_ENONFINITE for a
+ * non-finite norm.  Section 2.4 Stage 1 and Stage 3 ("forced to zero using the U-Net multigrid
+ * solver"). */
+int nn4_pressure_solve(nn4_plan p, const double* b, double* x, double rtol, int32_t max_iters,
+                       nn4_solve_info* info, void* stream);
+
+/* The same solve with host arrays: b_host and x_host are dense [nz][ny][nx] FP64 arrays in
+ * host memory (pinned for full copy speed); they are copied in and the solution copied out
+ * through plan-owned device buffers inside the call. */
+int nn4_pressure_solve_host(nn4_plan p, const double* b_host, double* x_host, double rtol,
+                            int32_t max_iters, nn4_solve_info* info, void* stream);
+
+/* ----------------------------------------------------------------- diagnostics */
+
+const char* nn4_last_error(void);
+
+/* Reads and clears the device error word: NN4_OK, NN4_ETIMEOUT or NN4_EBOUNDS. Synchronises. */
+int nn4_device_error(void);
+
+const char* nn4_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NN4_H */

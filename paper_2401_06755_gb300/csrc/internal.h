@@ -1,0 +1,87 @@
+// Host-side declarations shared between the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nn4.h"
+
+namespace nn4 {
+
+// Interior Q1 stencil on a mirror-extended field, by neighbour class: c[a + 2b + 4c] multiplies
+// the sum over the 2^(a+b+c) neighbours offset by +-1 along the axes flagged a (x), b (y), c (z).
+struct Coef8 {
+  double c[8];
+};
+
+// Geometry of one level as the kernels see it.
+struct LevelGeom {
+  int nx, ny, nz;
+  long long pitch;  // row pitch in elements of the array this geometry is used with
+  int dir[6];       // 1 where the face is Dirichlet (x-, x+, y-, y+, z-, z+)
+};
+
+// OP_APPLY: out = A x.  OP_RESIDUAL: out = b - A x (0 at Dirichlet nodes), norm2 += out^2.
+// OP_JACOBI: out = x + omega D^-1 (b - A x) (x at Dirichlet nodes).
+// OP_MATVEC: out = A x (0 at Dirichlet nodes), norm2 += x.out, dot2 += x.b.
+enum PassOp { OP_APPLY = 0, OP_RESIDUAL = 1, OP_JACOBI = 2, OP_MATVEC = 3 };
+
+struct PassArgs {
+  LevelGeom g;
+  Coef8 L;
+  double omega;
+  const void* b;     // right-hand side (OP_RESIDUAL, OP_JACOBI), pitch g.pitch
+  void* out;         // y / r / x_out, pitch g.pitch
+  double* norm2;     // optional: += sum out^2 (OP_RESIDUAL) or x.out (OP_MATVEC)
+  double* dot2;      // OP_MATVEC: += x.b
+  int zchunk;        // output planes per block
+};
+
+// Stencil pass launch configuration (chosen by the autotuner or by default).
+struct PassCfg {
+  int ry;      // outputs per thread along y
+  int tyt;     // threads along y (x is always one warp of 32)
+  int stages;  // TMA pipeline depth (planes in flight)
+  int zchunk;  // output planes per block
+};
+
+// ---------------------------------------------------------------- helpers (api.cu)
+Coef8 stencil_coef(const double h[3]);
+int set_error(int code, const std::string& msg);
+int check_cuda(cudaError_t e, const char* what);
+bool make_tmap_3d(CUtensorMap* map, nn4_dtype dt, const void* base, int nx, int ny, int nz,
+                  long long pitch, int box_x, int box_y);
+size_t dtype_size(nn4_dtype dt);
+
+// Per-unit device error words (read and cleared).
+unsigned int stencil_error_word();
+
+// ---------------------------------------------------------------- launchers
+// stencil.cu: constant coefficient (k == nullptr) or Eq. k-T (k given).  x and k are read with
+// TMA (their tensor maps are built here unless maps are given).
+int launch_pass(nn4_dtype dt, int op, const PassArgs& a, const void* x, const void* k,
+                const PassCfg& cfg, cudaStream_t s, const CUtensorMap* mx = nullptr,
+                const CUtensorMap* mk = nullptr);
+PassCfg default_pass_cfg(nn4_dtype dt, bool vc, const LevelGeom& g);
+int pass_box(nn4_dtype dt, const PassCfg& cfg, int* box_x, int* box_y);
+
+// transfer.cu
+int launch_restrict(nn4_dtype dt, const void* rf, const LevelGeom& gf, void* rc,
+                    const LevelGeom& gc, cudaStream_t s);
+int launch_prolong(nn4_dtype dt, const void* ec, const LevelGeom& gc, void* ef,
+                   const LevelGeom& gf, int accumulate, cudaStream_t s);
+// ef = base + P ec (base may be NULL for 0; may alias ef).  Fine Dirichlet nodes get base (or 0).
+int launch_prolong_base(nn4_dtype dt, const void* ec, const LevelGeom& gc, void* ef, const void* base,
+                        const LevelGeom& gf, cudaStream_t s);
+
+// coarse.cu: e = Ainv r on the coarsest level (FP64 matrix over the free nodes, whose grid
+// offsets are listed in `free_idx`).  Non-free nodes of e are set to 0; with `accumulate`,
+// e += Ainv r at free nodes and other nodes are left alone.
+int launch_coarse_solve(nn4_dtype dt, const double* ainv, const int* free_idx, int nfree,
+                        const void* r, void* e, const LevelGeom& g, int accumulate, cudaStream_t s);
+
+}  // namespace nn4

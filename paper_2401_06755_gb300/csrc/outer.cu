@@ -1,0 +1,159 @@
+// Pointwise FP64 kernels of the outer loop of the pressure solve: defect-correction update,
+// conversion of the FP64 residual to the inner storage type, and the flexible-CG recurrences
+// (Notay 2000) with their dot products.  All sums are accumulated in FP64.
+#include "common.cuh"
+#include "internal.h"
+#include "outer.h"
+
+namespace nn4 {
+namespace {
+
+// Grid-stride loop over the nodes of a pitched field: one thread per x, rows spread over the grid.
+#define NN4_FOR_NODES(G)                                                                    \
+  for (long long row = blockIdx.x * (long long)blockDim.y + threadIdx.y;                     \
+       row < (long long)(G).ny * (G).nz; row += (long long)gridDim.x * blockDim.y)           \
+    for (int i = threadIdx.x; i < (G).nx; i += blockDim.x)
+
+__device__ __forceinline__ bool dirichlet_row(const LevelGeom& g, long long row, int i) {
+  const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+  return (g.dir[0] && i == 0) || (g.dir[1] && i == g.nx - 1) || (g.dir[2] && j == 0) ||
+         (g.dir[3] && j == g.ny - 1) || (g.dir[4] && k == 0) || (g.dir[5] && k == g.nz - 1);
+}
+
+template <typename T>
+__global__ void k_add_correction(double* __restrict__ x, LevelGeom g64, const T* __restrict__ e, LevelGeom gT) {
+  NN4_FOR_NODES(g64) {
+    x[row * g64.pitch + i] += (double)to_acc(e[row * gT.pitch + i]);
+  }
+}
+
+template <typename T>
+__global__ void k_to_inner(const double* __restrict__ r, LevelGeom g64, T* __restrict__ rT, LevelGeom gT) {
+  NN4_FOR_NODES(g64) { rT[row * gT.pitch + i] = from_acc<T>(r[row * g64.pitch + i]); }
+}
+
+__global__ void k_norm_masked(const double* __restrict__ v, LevelGeom g, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  NN4_FOR_NODES(g) {
+    if (!dirichlet_row(g, row, i)) {
+      const double t = v[row * g.pitch + i];
+      s += t * t;
+    }
+  }
+  block_sum_atomic(s, out, red);
+}
+
+// out += sum z_i * q_i (z in the inner type, q FP64)
+template <typename T>
+__global__ void k_dot_zq(const T* __restrict__ z, LevelGeom gT, const double* __restrict__ q, LevelGeom g64,
+                         double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  NN4_FOR_NODES(g64) { s += (double)to_acc(z[row * gT.pitch + i]) * q[row * g64.pitch + i]; }
+  block_sum_atomic(s, out, red);
+}
+
+// p = z - beta p_old with beta = zq / pq_old
+template <typename T>
+__global__ void k_new_direction(const T* __restrict__ z, LevelGeom gT, const double* __restrict__ p_old,
+                                double* __restrict__ p, LevelGeom g64, const double* zq, const double* pq_old) {
+  const double beta = *zq / *pq_old;
+  NN4_FOR_NODES(g64) {
+    const long long o = row * g64.pitch + i;
+    p[o] = (double)to_acc(z[row * gT.pitch + i]) - beta * p_old[o];
+  }
+}
+
+// alpha = pr / pq; x += alpha p; r -= alpha q; rT = r; norm += r^2 (free nodes)
+template <typename T>
+__global__ void k_fcg_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                             const double* __restrict__ q, LevelGeom g64, T* __restrict__ rT, LevelGeom gT,
+                             const double* pr, const double* pq, double* norm2) {
+  __shared__ double red[32];
+  const double alpha = *pr / *pq;
+  double s = 0.0;
+  NN4_FOR_NODES(g64) {
+    const long long o = row * g64.pitch + i;
+    x[o] += alpha * p[o];
+    const double rn = r[o] - alpha * q[o];
+    r[o] = rn;
+    if (rT) rT[row * gT.pitch + i] = from_acc<T>(rn);
+    s += rn * rn;
+  }
+  block_sum_atomic(s, norm2, red);
+}
+
+dim3 pw_grid(const LevelGeom& g) {
+  long long rows = (long long)g.ny * g.nz;
+  long long blocks = (rows + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  return dim3((unsigned)blocks);
+}
+const dim3 kPwBlock(32, 8);
+
+template <typename T>
+int add_correction_t(double* x, const LevelGeom& g64, const void* e, const LevelGeom& gT, cudaStream_t s) {
+  k_add_correction<T><<<pw_grid(g64), kPwBlock, 0, s>>>(x, g64, static_cast<const T*>(e), gT);
+  return check_cuda(cudaGetLastError(), "add correction");
+}
+template <typename T>
+int to_inner_t(const double* r, const LevelGeom& g64, void* rT, const LevelGeom& gT, cudaStream_t s) {
+  k_to_inner<T><<<pw_grid(g64), kPwBlock, 0, s>>>(r, g64, static_cast<T*>(rT), gT);
+  return check_cuda(cudaGetLastError(), "to inner");
+}
+template <typename T>
+int dot_zq_t(const void* z, const LevelGeom& gT, const double* q, const LevelGeom& g64, double* out, cudaStream_t s) {
+  k_dot_zq<T><<<pw_grid(g64), kPwBlock, 0, s>>>(static_cast<const T*>(z), gT, q, g64, out);
+  return check_cuda(cudaGetLastError(), "dot");
+}
+template <typename T>
+int new_direction_t(const void* z, const LevelGeom& gT, const double* p_old, double* p, const LevelGeom& g64,
+                    const double* zq, const double* pq_old, cudaStream_t s) {
+  k_new_direction<T><<<pw_grid(g64), kPwBlock, 0, s>>>(static_cast<const T*>(z), gT, p_old, p, g64, zq, pq_old);
+  return check_cuda(cudaGetLastError(), "new direction");
+}
+template <typename T>
+int fcg_update_t(double* x, double* r, const double* p, const double* q, const LevelGeom& g64, void* rT,
+                 const LevelGeom& gT, const double* pr, const double* pq, double* norm2, cudaStream_t s) {
+  k_fcg_update<T><<<pw_grid(g64), kPwBlock, 0, s>>>(x, r, p, q, g64, static_cast<T*>(rT), gT, pr, pq, norm2);
+  return check_cuda(cudaGetLastError(), "fcg update");
+}
+
+}  // namespace
+
+#define NN4_DISPATCH(dt, call)                         \
+  switch (dt) {                                        \
+    case NN4_F64: { using T = double; return call; }   \
+    case NN4_F32: { using T = float; return call; }    \
+    case NN4_BF16: { using T = bf16; return call; }    \
+  }                                                    \
+  return set_error(NN4_EINVAL, "bad dtype");
+
+int launch_add_correction(nn4_dtype dt, double* x, const LevelGeom& g64, const void* e, const LevelGeom& gT,
+                          cudaStream_t s) {
+  NN4_DISPATCH(dt, add_correction_t<T>(x, g64, e, gT, s))
+}
+int launch_to_inner(nn4_dtype dt, const double* r, const LevelGeom& g64, void* rT, const LevelGeom& gT,
+                    cudaStream_t s) {
+  NN4_DISPATCH(dt, to_inner_t<T>(r, g64, rT, gT, s))
+}
+int launch_norm_masked(const double* v, const LevelGeom& g, double* out, cudaStream_t s) {
+  k_norm_masked<<<pw_grid(g), kPwBlock, 0, s>>>(v, g, out);
+  return check_cuda(cudaGetLastError(), "norm");
+}
+int launch_dot_zq(nn4_dtype dt, const void* z, const LevelGeom& gT, const double* q, const LevelGeom& g64,
+                  double* out, cudaStream_t s) {
+  NN4_DISPATCH(dt, dot_zq_t<T>(z, gT, q, g64, out, s))
+}
+int launch_new_direction(nn4_dtype dt, const void* z, const LevelGeom& gT, const double* p_old, double* p,
+                         const LevelGeom& g64, const double* zq, const double* pq_old, cudaStream_t s) {
+  NN4_DISPATCH(dt, new_direction_t<T>(z, gT, p_old, p, g64, zq, pq_old, s))
+}
+int launch_fcg_update(nn4_dtype dt, double* x, double* r, const double* p, const double* q, const LevelGeom& g64,
+                      void* rT, const LevelGeom& gT, const double* pr, const double* pq, double* norm2,
+                      cudaStream_t s) {
+  NN4_DISPATCH(dt, fcg_update_t<T>(x, r, p, q, g64, rT, gT, pr, pq, norm2, s))
+}
+
+}  // namespace nn4

@@ -1,0 +1,746 @@
+// Multigrid plan: hierarchy, coarsest-level inverse, sawtooth V-cycle and pressure solves.
+//
+// The cycle follows the reading of the paper's U-Net multigrid (Section 2.4, multigrid figure):
+// residual on the finest level, stride-2 restriction to the coarsest level, exact coarsest
+// solve, then on every level on the way up prolongation followed by one weighted-Jacobi sweep.
+// The solve wraps inner cycles (stored in FP64, FP32 or BF16) in an FP64 outer loop: plain
+// defect correction (the paper's repeated cycles) or flexible CG.  Every outer iteration is one
+// CUDA graph (captured at the first solve), so a solve is a few graph launches plus one
+// residual-norm readback per `check_every` iterations.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "galerkin.h"
+#include "internal.h"
+#include "outer.h"
+
+namespace nn4 {
+
+LevelGeom geom_of(const nn4_grid* g);
+
+namespace {
+
+struct Level {
+  LevelGeom g;      // inner-dtype pitch
+  double h[3];
+  Coef8 L;
+  PassCfg cfg;
+  void* r = nullptr;  // right-hand side of this level
+  void* e = nullptr;  // correction (output of the Jacobi sweep)
+  void* t = nullptr;  // prolongated correction / fine residual (input of the Jacobi sweep)
+  CUtensorMap tm_t{}, tm_e{};
+  void* a27 = nullptr;  // Galerkin coefficients (coefficient field, levels >= 1)
+  void* k = nullptr;    // coefficient field in the inner type (level 0)
+  CUtensorMap tm_k{};
+};
+
+}  // namespace
+
+struct PlanImpl {
+  nn4_grid grid;
+  nn4_plan_opts o;
+  nn4_dtype T;
+  bool vc = false;
+  std::vector<Level> lv;
+  // coarsest level
+  double* ainv = nullptr;
+  int* free_idx = nullptr;
+  int nfree = 0;
+  // FP64 outer loop (pitch grid.pitch)
+  LevelGeom g64;
+  Coef8 L64;
+  PassCfg cfg64;
+  double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *p64[2] = {nullptr, nullptr},
+         *q64[2] = {nullptr, nullptr}, *k64 = nullptr;
+  CUtensorMap tm_x64{}, tm_p64[2]{}, tm_k64{};
+  // device scalars: [0] ||r||^2 (current), [1] ||b||^2, [2] z.q, [3..4] p.q by parity,
+  // [5..6] p.r by parity; then the per-iteration history of ||r||^2
+  double* scal = nullptr;
+  double* hist = nullptr;
+  int hist_cap = 0;
+  double* host_hist = nullptr;  // pinned
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t graph_stream = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int alloc(PlanImpl* P, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return check_cuda(e, "cudaMalloc (plan)");
+  P->allocs.push_back(*p);
+  return check_cuda(cudaMemset(*p, 0, bytes), "cudaMemset (plan)");
+}
+
+size_t field_bytes(const LevelGeom& g, nn4_dtype dt) {
+  return (size_t)g.pitch * g.ny * g.nz * dtype_size(dt);
+}
+
+// ---------------------------------------------------------------- host dense algebra
+// Constant-coefficient operator on a level, applied on the host to a dense vector (mirror rule
+// for natural faces as in the kernels), used only to assemble the coarsest matrix.
+void host_apply_const(const Level& L, const std::vector<double>& x, std::vector<double>& y) {
+  const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz;
+  auto m = [](int i, int n) { return i < 0 ? -i : (i >= n ? 2 * (n - 1) - i : i); };
+  auto hc = [](int i, int n) { return 0.5 * ((i > 0) + (i < n - 1)); };
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double s = 0.0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int cls = (dx != 0) + 2 * (dy != 0) + 4 * (dz != 0);
+              s += L.L.c[cls] * x[m(i + dx, nx) + nx * (m(j + dy, ny) + ny * m(k + dz, nz))];
+            }
+        y[i + nx * (j + ny * k)] = hc(i, nx) * hc(j, ny) * hc(k, nz) * s;
+      }
+}
+
+// In-place inverse of a dense n x n matrix by Gauss-Jordan elimination with partial pivoting.
+bool invert(std::vector<double>& A, int n) {
+  std::vector<double> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+    if (A[(size_t)piv * n + c] == 0.0) return false;
+    if (piv != c)
+      for (int t = 0; t < n; ++t) {
+        std::swap(A[(size_t)c * n + t], A[(size_t)piv * n + t]);
+        std::swap(I[(size_t)c * n + t], I[(size_t)piv * n + t]);
+      }
+    const double d = 1.0 / A[(size_t)c * n + c];
+    for (int t = 0; t < n; ++t) {
+      A[(size_t)c * n + t] *= d;
+      I[(size_t)c * n + t] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = A[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int t = 0; t < n; ++t) {
+        A[(size_t)r * n + t] -= f * A[(size_t)c * n + t];
+        I[(size_t)r * n + t] -= f * I[(size_t)c * n + t];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+// Operator of Eq. k-T on a level, applied on the host to a dense vector (mirror rule), for the
+// coarsest matrix when the fine grid is already the coarsest level.
+void host_apply_kt(const Level& L, const std::vector<double>& kf, const std::vector<double>& x,
+                   std::vector<double>& y) {
+  const int N = (int)x.size();
+  std::vector<double> kx(N), Lx(N), Lkx(N), Lk(N);
+  for (int t = 0; t < N; ++t) kx[t] = kf[t] * x[t];
+  host_apply_const(L, x, Lx);
+  host_apply_const(L, kx, Lkx);
+  host_apply_const(L, kf, Lk);
+  for (int t = 0; t < N; ++t) y[t] = 0.5 * (Lkx[t] + kf[t] * Lx[t] - x[t] * Lk[t]);
+}
+
+}  // namespace
+
+int build_galerkin_hierarchy(PlanImpl* P, std::vector<double>& dense) {
+  const nn4_dtype ct = P->T == NN4_F64 ? NN4_F64 : NN4_F32;
+  const size_t cs = dtype_size(ct);
+  int rc;
+  void* prev = nullptr;
+  LevelGeom gprev{};
+  for (size_t l = 1; l < P->lv.size(); ++l) {
+    Level& L = P->lv[l];
+    const size_t n27 = (size_t)kA27 * L.g.pitch * L.g.ny * L.g.nz;
+    void* tmp = nullptr;
+    if ((rc = alloc(P, &tmp, n27 * cs))) return rc;
+    if (l == 1)
+      rc = launch_galerkin_from_k(ct, P->k64, P->g64, P->lv[0].h, tmp, L.g, 0);
+    else
+      rc = launch_galerkin_next(ct, prev, gprev, tmp, L.g, 0);
+    if (rc) return rc;
+    if (P->T == ct) {
+      L.a27 = tmp;
+    } else {
+      if ((rc = alloc(P, &L.a27, n27 * dtype_size(P->T)))) return rc;
+      if ((rc = launch_convert27(ct, tmp, P->T, L.a27, L.g, 0))) return rc;
+    }
+    prev = tmp;
+    gprev = L.g;
+  }
+  Level& C = P->lv.back();
+  const int nx = C.g.nx, ny = C.g.ny, nz = C.g.nz, N = nx * ny * nz;
+  dense.assign((size_t)N * N, 0.0);
+  if (P->lv.size() == 1) {
+    std::vector<double> kf(N), k64((size_t)P->g64.pitch * ny * nz);
+    if ((rc = check_cuda(cudaMemcpy(k64.data(), P->k64, k64.size() * 8, cudaMemcpyDeviceToHost), "copy k")))
+      return rc;
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) kf[i + nx * (j + ny * k)] = k64[i + P->g64.pitch * (j + (size_t)ny * k)];
+    std::vector<double> x(N, 0.0), y(N);
+    for (int j = 0; j < N; ++j) {
+      x[j] = 1.0;
+      host_apply_kt(C, kf, x, y);
+      for (int i = 0; i < N; ++i) dense[(size_t)i * N + j] = y[i];
+      x[j] = 0.0;
+    }
+    return NN4_OK;
+  }
+  const size_t plane = (size_t)C.g.pitch * ny * nz;
+  std::vector<char> host(kA27 * plane * cs);
+  if ((rc = check_cuda(cudaMemcpy(host.data(), prev, host.size(), cudaMemcpyDeviceToHost), "copy coarsest")))
+    return rc;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        for (int d = 0; d < kA27; ++d) {
+          const int i2 = i + d % 3 - 1, j2 = j + (d / 3) % 3 - 1, k2 = k + d / 9 - 1;
+          if (i2 < 0 || i2 >= nx || j2 < 0 || j2 >= ny || k2 < 0 || k2 >= nz) continue;
+          const size_t o = d * plane + i + C.g.pitch * (j + (size_t)ny * k);
+          const double v = ct == NN4_F64 ? reinterpret_cast<const double*>(host.data())[o]
+                                         : (double)reinterpret_cast<const float*>(host.data())[o];
+          dense[(size_t)(i + nx * (j + ny * k)) * N + (i2 + nx * (j2 + ny * k2))] = v;
+        }
+  return NN4_OK;
+}
+
+namespace {
+
+bool is_dir(const LevelGeom& g, int i, int j, int k) {
+  return (g.dir[0] && i == 0) || (g.dir[1] && i == g.nx - 1) || (g.dir[2] && j == 0) ||
+         (g.dir[3] && j == g.ny - 1) || (g.dir[4] && k == 0) || (g.dir[5] && k == g.nz - 1);
+}
+
+// Dense (pseudo-)inverse of the coarsest operator over its free nodes.
+int build_coarsest(PlanImpl* P, const std::vector<double>& dense_all) {
+  Level& C = P->lv.back();
+  const int nx = C.g.nx, ny = C.g.ny, nz = C.g.nz, N = nx * ny * nz;
+  std::vector<int> free_lin, free_off;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        if (!is_dir(C.g, i, j, k)) {
+          free_lin.push_back(i + nx * (j + ny * k));
+          free_off.push_back((int)(i + C.g.pitch * (j + (long long)ny * k)));
+        }
+  const int n = (int)free_lin.size();
+  if (n > 1024) return set_error(NN4_EUNSUPPORTED, "coarsest level has more than 1024 free nodes");
+  if (n == 0) return set_error(NN4_EINVAL, "coarsest level has no free node");
+  std::vector<double> A((size_t)n * n);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) A[(size_t)a * n + b] = dense_all[(size_t)free_lin[a] * N + free_lin[b]];
+  bool singular = true;
+  for (int f = 0; f < 6; ++f) singular = singular && !C.g.dir[f];
+  if (singular)  // null space = constants: pinv(A) = (A + J/n)^-1 - J/n
+    for (auto& v : A) v += 1.0 / n;
+  if (!invert(A, n)) return set_error(NN4_EINVAL, "coarsest operator is singular");
+  if (singular)
+    for (auto& v : A) v -= 1.0 / n;
+  int rc;
+  if ((rc = alloc(P, (void**)&P->ainv, sizeof(double) * n * n))) return rc;
+  if ((rc = alloc(P, (void**)&P->free_idx, sizeof(int) * n))) return rc;
+  if ((rc = check_cuda(cudaMemcpy(P->ainv, A.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice), "copy ainv")))
+    return rc;
+  if ((rc = check_cuda(cudaMemcpy(P->free_idx, free_off.data(), sizeof(int) * n, cudaMemcpyHostToDevice), "copy idx")))
+    return rc;
+  P->nfree = n;
+  return NN4_OK;
+}
+
+// ---------------------------------------------------------------- the cycle
+// One V-cycle on A e = r at level 0.  `first`: e = 0 on entry (the fine residual is r itself).
+// rhs/e/t pointers and maps of level 0 are taken from the level (inner solve) or given
+// (standalone cycle on caller arrays).
+struct Fine {
+  const void* r;
+  void* e;
+  const CUtensorMap* tm_e;
+};
+
+int run_pass(PlanImpl* P, int l, int op, const void* x, const CUtensorMap* mx, const void* b, void* out,
+             cudaStream_t s, double* norm2 = nullptr) {
+  Level& L = P->lv[l];
+  PassArgs a{};
+  a.g = L.g;
+  a.L = L.L;
+  a.omega = P->o.omega;
+  a.b = b;
+  a.out = out;
+  a.norm2 = norm2;
+  a.zchunk = L.cfg.zchunk;
+  if (P->vc && l > 0) return launch_pass27(P->T, op, a, x, L.a27, s);
+  const bool vc0 = P->vc && l == 0;
+  return launch_pass(P->T, op, a, x, vc0 ? L.k : nullptr, L.cfg, s, mx, vc0 ? &L.tm_k : nullptr);
+}
+
+int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
+  const int nl = (int)P->lv.size();
+  const nn4_dtype T = P->T;
+  int rc;
+  Level& L0 = P->lv[0];
+  if (nl == 1) {  // the fine grid is the coarsest: e += A^-1 (r - A e)
+    if (first) return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, F.r, F.e, L0.g, 0, s);
+    if ((rc = run_pass(P, 0, OP_RESIDUAL, F.e, F.tm_e, F.r, L0.t, s))) return rc;
+    return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, L0.t, F.e, L0.g, 1, s);
+  }
+  // down: fine residual, then restriction to the coarsest level
+  const void* r0 = F.r;
+  if (!first) {
+    if ((rc = run_pass(P, 0, OP_RESIDUAL, F.e, F.tm_e, F.r, L0.t, s))) return rc;
+    r0 = L0.t;
+  }
+  if ((rc = launch_restrict(T, r0, L0.g, P->lv[1].r, P->lv[1].g, s))) return rc;
+  for (int l = 1; l + 1 < nl; ++l)
+    if ((rc = launch_restrict(T, P->lv[l].r, P->lv[l].g, P->lv[l + 1].r, P->lv[l + 1].g, s))) return rc;
+  Level& C = P->lv[nl - 1];
+  if ((rc = launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, C.r, C.e, C.g, 0, s))) return rc;
+  // up: prolongation then one Jacobi sweep per level
+  for (int l = nl - 2; l >= 1; --l) {
+    Level& L = P->lv[l];
+    if ((rc = launch_prolong_base(T, P->lv[l + 1].e, P->lv[l + 1].g, L.t, nullptr, L.g, s))) return rc;
+    if ((rc = run_pass(P, l, OP_JACOBI, L.t, &L.tm_t, L.r, L.e, s))) return rc;
+  }
+  if ((rc = launch_prolong_base(T, P->lv[1].e, P->lv[1].g, L0.t, first ? nullptr : F.e, L0.g, s))) return rc;
+  return run_pass(P, 0, OP_JACOBI, L0.t, &L0.tm_t, F.r, F.e, s);
+}
+
+// ---------------------------------------------------------------- outer iterations
+int inner_solve(PlanImpl* P, cudaStream_t s) {
+  Level& L0 = P->lv[0];
+  Fine F{L0.r, L0.e, &L0.tm_e};
+  int rc;
+  for (int c = 0; c < P->o.inner_cycles; ++c)
+    if ((rc = vcycle_impl(P, F, c == 0, s))) return rc;
+  return NN4_OK;
+}
+
+int outer_residual(PlanImpl* P, cudaStream_t s, double* norm2) {
+  // r64 = b - A x (FP64) and its squared norm
+  PassArgs a{};
+  a.g = P->g64;
+  a.L = P->L64;
+  a.b = P->b64;
+  a.out = P->r64;
+  a.norm2 = norm2;
+  a.zchunk = P->cfg64.zchunk;
+  int rc;
+  if ((rc = check_cuda(cudaMemsetAsync(norm2, 0, sizeof(double), s), "zero norm"))) return rc;
+  return launch_pass(NN4_F64, OP_RESIDUAL, a, P->x64, P->vc ? P->k64 : nullptr, P->cfg64, s, &P->tm_x64,
+                     P->vc ? &P->tm_k64 : nullptr);
+}
+
+// One defect-correction iteration: rT = r; e = cycles(rT); x += e; r = b - A x (norm -> scal[0]).
+int iteration_cycles(PlanImpl* P, cudaStream_t s) {
+  Level& L0 = P->lv[0];
+  int rc;
+  if (P->T != NN4_F64 && (rc = launch_to_inner(P->T, P->r64, P->g64, L0.r, L0.g, s))) return rc;
+  if ((rc = inner_solve(P, s))) return rc;
+  if ((rc = launch_add_correction(P->T, P->x64, P->g64, L0.e, L0.g, s))) return rc;
+  return outer_residual(P, s, P->scal + 0);
+}
+
+// One flexible-CG iteration with parity `par` (p, q buffers and p.q, p.r slots alternate).
+int iteration_fcg(PlanImpl* P, int par, cudaStream_t s) {
+  Level& L0 = P->lv[0];
+  const int old = 1 - par;
+  int rc;
+  if ((rc = inner_solve(P, s))) return rc;  // z = L0.e from rT = L0.r
+  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 2, 0, sizeof(double), s), "zero zq"))) return rc;
+  if ((rc = launch_dot_zq(P->T, L0.e, L0.g, P->q64[old], P->g64, P->scal + 2, s))) return rc;
+  if ((rc = launch_new_direction(P->T, L0.e, L0.g, P->p64[old], P->p64[par], P->g64, P->scal + 2,
+                                 P->scal + 3 + old, s)))
+    return rc;
+  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 3 + par, 0, sizeof(double), s), "zero pq"))) return rc;
+  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 5 + par, 0, sizeof(double), s), "zero pr"))) return rc;
+  PassArgs a{};
+  a.g = P->g64;
+  a.L = P->L64;
+  a.b = P->r64;
+  a.out = P->q64[par];
+  a.norm2 = P->scal + 3 + par;
+  a.dot2 = P->scal + 5 + par;
+  a.zchunk = P->cfg64.zchunk;
+  if ((rc = launch_pass(NN4_F64, OP_MATVEC, a, P->p64[par], P->vc ? P->k64 : nullptr, P->cfg64, s,
+                        &P->tm_p64[par], P->vc ? &P->tm_k64 : nullptr)))
+    return rc;
+  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 0, 0, sizeof(double), s), "zero norm"))) return rc;
+  return launch_fcg_update(P->T, P->x64, P->r64, P->p64[par], P->q64[par], P->g64,
+                           P->T == NN4_F64 ? nullptr : L0.r, L0.g, P->scal + 5 + par, P->scal + 3 + par,
+                           P->scal + 0, s);
+}
+
+int iteration(PlanImpl* P, int it, cudaStream_t s) {
+  return P->o.outer == NN4_OUTER_FCG ? iteration_fcg(P, it & 1, s) : iteration_cycles(P, s);
+}
+
+int ensure_graphs(PlanImpl* P) {
+  if (!P->o.use_graph || P->graph[0]) return NN4_OK;
+  int rc;
+  if (!P->graph_stream &&
+      (rc = check_cuda(cudaStreamCreateWithFlags(&P->graph_stream, cudaStreamNonBlocking), "graph stream")))
+    return rc;
+  const int ng = P->o.outer == NN4_OUTER_FCG ? 2 : 1;
+  for (int par = 0; par < ng; ++par) {
+    cudaGraph_t g;
+    if ((rc = check_cuda(cudaStreamBeginCapture(P->graph_stream, cudaStreamCaptureModeThreadLocal), "begin capture")))
+      return rc;
+    rc = iteration(P, par, P->graph_stream);
+    cudaError_t e = cudaStreamEndCapture(P->graph_stream, &g);
+    if (rc) return rc;
+    if ((rc = check_cuda(e, "end capture"))) return rc;
+    e = cudaGraphInstantiate(&P->graph[par], g, 0);
+    cudaGraphDestroy(g);
+    if ((rc = check_cuda(e, "graph instantiate"))) return rc;
+  }
+  return NN4_OK;
+}
+
+int launch_iteration(PlanImpl* P, int it, cudaStream_t s) {
+  if (P->o.use_graph) {
+    const int par = P->o.outer == NN4_OUTER_FCG ? (it & 1) : 0;
+    return check_cuda(cudaGraphLaunch(P->graph[par], s), "graph launch");
+  }
+  return iteration(P, it, s);
+}
+
+int make_level_maps(PlanImpl* P, Level& L) {
+  int bx, by;
+  pass_box(P->T, L.cfg, &bx, &by);
+  if (!make_tmap_3d(&L.tm_t, P->T, L.t, L.g.nx, L.g.ny, L.g.nz, L.g.pitch, bx, by) ||
+      !make_tmap_3d(&L.tm_e, P->T, L.e, L.g.nx, L.g.ny, L.g.nz, L.g.pitch, bx, by))
+    return set_error(NN4_ECUDA, "tensor map encode failed");
+  if (L.k && !make_tmap_3d(&L.tm_k, P->T, L.k, L.g.nx, L.g.ny, L.g.nz, L.g.pitch, bx, by))
+    return set_error(NN4_ECUDA, "tensor map encode failed (k)");
+  return NN4_OK;
+}
+
+void destroy(PlanImpl* P) {
+  if (!P) return;
+  for (auto& g : P->graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (P->graph_stream) cudaStreamDestroy(P->graph_stream);
+  for (void* p : P->allocs) cudaFree(p);
+  if (P->host_hist) cudaFreeHost(P->host_hist);
+  delete P;
+}
+
+int validate_plan_grid(const nn4_grid* g) {
+  if (!g) return set_error(NN4_EINVAL, "grid is NULL");
+  for (int d = 0; d < 3; ++d) {
+    if (g->n[d] < 3) return set_error(NN4_EINVAL, "plans need at least 3 nodes per axis");
+    if (!(g->h[d] > 0.0)) return set_error(NN4_EINVAL, "grid spacing must be positive");
+  }
+  for (int f = 0; f < 6; ++f)
+    if (g->bc[f] != NN4_BC_DIRICHLET && g->bc[f] != NN4_BC_NATURAL) return set_error(NN4_EINVAL, "bad face condition");
+  if (g->pitch < g->n[0] || (g->pitch * 8) % 16 != 0) return set_error(NN4_EINVAL, "bad FP64 pitch");
+  return NN4_OK;
+}
+
+int solve_device(PlanImpl* P, double rtol, int32_t max_iters, nn4_solve_info* info, cudaStream_t s) {
+  int rc;
+  if (max_iters < 0) return set_error(NN4_EINVAL, "max_iters must be >= 0");
+  if (max_iters + 1 > P->hist_cap) {
+    // grow the history buffers (outside any capture)
+    const int cap = max_iters + 64;
+    double* h = nullptr;
+    double* hh = nullptr;
+    if ((rc = check_cuda(cudaMalloc(&h, sizeof(double) * cap), "history alloc"))) return rc;
+    if ((rc = check_cuda(cudaMallocHost(&hh, sizeof(double) * cap), "history host alloc"))) {
+      cudaFree(h);
+      return rc;
+    }
+    P->allocs.push_back(h);
+    if (P->host_hist) cudaFreeHost(P->host_hist);
+    P->hist = h;
+    P->host_hist = hh;
+    P->hist_cap = cap;
+  }
+  if ((rc = ensure_graphs(P))) return rc;
+  // ||b||^2 over free nodes, initial residual
+  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 1, 0, sizeof(double), s), "zero"))) return rc;
+  if ((rc = launch_norm_masked(P->b64, P->g64, P->scal + 1, s))) return rc;
+  if ((rc = outer_residual(P, s, P->scal + 0))) return rc;
+  if (P->o.outer == NN4_OUTER_FCG) {
+    // r64 holds the residual; rT for the first inner solve; p_old = q_old = 0, p.q_old = 1
+    if (P->T != NN4_F64 && (rc = launch_to_inner(P->T, P->r64, P->g64, P->lv[0].r, P->lv[0].g, s))) return rc;
+    if (P->T == NN4_F64 &&
+        (rc = check_cuda(cudaMemcpyAsync(P->lv[0].r, P->r64, field_bytes(P->g64, NN4_F64), cudaMemcpyDeviceToDevice, s),
+                         "copy r")))
+      return rc;
+    const size_t fb = field_bytes(P->g64, NN4_F64);
+    for (int t = 0; t < 2; ++t) {
+      if ((rc = check_cuda(cudaMemsetAsync(P->p64[t], 0, fb, s), "zero p"))) return rc;
+      if ((rc = check_cuda(cudaMemsetAsync(P->q64[t], 0, fb, s), "zero q"))) return rc;
+    }
+    const double one[2] = {1.0, 1.0};
+    if ((rc = check_cuda(cudaMemcpyAsync(P->scal + 3, one, sizeof(one), cudaMemcpyHostToDevice, s), "init pq")))
+      return rc;
+  }
+  if ((rc = check_cuda(cudaMemcpyAsync(P->hist, P->scal + 0, sizeof(double), cudaMemcpyDeviceToDevice, s), "hist")))
+    return rc;
+  double bb = 0.0;
+  if ((rc = check_cuda(cudaMemcpyAsync(P->host_hist, P->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s), "read")))
+    return rc;
+  if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) return rc;
+  bb = P->host_hist[1];
+  double rr = P->host_hist[0];
+  const double bn = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+  if (!std::isfinite(rr) || !std::isfinite(bb)) return set_error(NN4_ENONFINITE, "non-finite initial residual");
+  int it = 0;
+  double rel = std::sqrt(rr) / bn;
+  const int every = P->o.check_every > 0 ? P->o.check_every : 1;
+  int status = NN4_OK;
+  bool fixed = rtol <= 0.0;  // rtol <= 0: run exactly max_iters iterations
+  while (it < max_iters && (fixed || rel > rtol)) {
+    const int todo = fixed ? max_iters - it : std::min(every, max_iters - it);
+    for (int t = 0; t < todo; ++t, ++it) {
+      if ((rc = launch_iteration(P, it, s))) return rc;
+      if ((rc = check_cuda(cudaMemcpyAsync(P->hist + it + 1, P->scal + 0, sizeof(double), cudaMemcpyDeviceToDevice, s),
+                           "hist")))
+        return rc;
+    }
+    if ((rc = check_cuda(cudaMemcpyAsync(P->host_hist, P->hist + it, sizeof(double), cudaMemcpyDeviceToHost, s), "read")))
+      return rc;
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) return rc;
+    if (!std::isfinite(P->host_hist[0])) {
+      status = set_error(NN4_ENONFINITE, "non-finite residual norm");
+      break;
+    }
+    rel = std::sqrt(P->host_hist[0]) / bn;
+  }
+  // final true residual (FCG keeps a recurrence)
+  if (P->o.outer == NN4_OUTER_FCG) {
+    if ((rc = outer_residual(P, s, P->scal + 0))) return rc;
+  }
+  std::vector<double> h(it + 1);
+  if ((rc = check_cuda(cudaMemcpyAsync(P->host_hist, P->scal + 0, sizeof(double), cudaMemcpyDeviceToHost, s), "read")))
+    return rc;
+  if ((rc = check_cuda(cudaMemcpyAsync(h.data(), P->hist, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, s), "read")))
+    return rc;
+  if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) return rc;
+  const double final_rel = std::sqrt(P->host_hist[0]) / bn;
+  if (info) {
+    info->iterations = it;
+    info->cycles = it * P->o.inner_cycles;
+    info->rel_res = final_rel;
+    if (info->history)
+      for (int t = 0; t <= it && t < info->history_len; ++t) info->history[t] = std::sqrt(h[t]) / bn;
+  }
+  if (status != NN4_OK) return status;
+  if (!std::isfinite(final_rel)) return set_error(NN4_ENONFINITE, "non-finite residual norm");
+  if (!fixed && final_rel > rtol) return set_error(NN4_ENOCONV, "iteration cap reached before the tolerance");
+  return NN4_OK;
+}
+
+}  // namespace
+}  // namespace nn4
+
+using namespace nn4;
+
+struct nn4_plan_s {
+  PlanImpl* impl;
+};
+
+extern "C" {
+
+void nn4_plan_opts_default(nn4_plan_opts* o) {
+  if (!o) return;
+  o->inner = NN4_F64;
+  o->inner_cycles = 1;
+  o->outer = NN4_OUTER_CYCLES;
+  o->omega = 2.0 / 3.0;
+  o->use_graph = 1;
+  o->check_every = 1;
+}
+
+int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opts, nn4_plan* out) {
+  if (!out) return set_error(NN4_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc;
+  if ((rc = validate_plan_grid(g))) return rc;
+  nn4_plan_opts o;
+  nn4_plan_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.inner != NN4_F64 && o.inner != NN4_F32 && o.inner != NN4_BF16) return set_error(NN4_EINVAL, "bad inner dtype");
+  if (o.inner_cycles < 1 || o.inner_cycles > 64) return set_error(NN4_EINVAL, "inner_cycles must be in 1..64");
+  if (o.outer != NN4_OUTER_CYCLES && o.outer != NN4_OUTER_FCG) return set_error(NN4_EINVAL, "bad outer method");
+  if (!(o.omega > 0.0 && o.omega < 2.0)) return set_error(NN4_EINVAL, "omega must lie in (0, 2)");
+  if (k && reinterpret_cast<uintptr_t>(k) % 16) return set_error(NN4_EINVAL, "k is not 16-byte aligned");
+
+  PlanImpl* P = new PlanImpl();
+  P->grid = *g;
+  P->o = o;
+  P->T = o.inner;
+  P->vc = k != nullptr;
+  P->g64 = geom_of(g);
+  P->L64 = stencil_coef(g->h);
+  P->cfg64 = default_pass_cfg(NN4_F64, P->vc, P->g64);
+
+  // hierarchy: halve while every axis is odd and >= 5
+  {
+    Level L;
+    L.g = P->g64;
+    L.g.pitch = nn4_row_pitch(g->n[0], P->T);
+    for (int d = 0; d < 3; ++d) L.h[d] = g->h[d];
+    P->lv.push_back(L);
+    while (true) {
+      const Level& f = P->lv.back();
+      if (!(f.g.nx >= 5 && f.g.ny >= 5 && f.g.nz >= 5 && (f.g.nx & 1) && (f.g.ny & 1) && (f.g.nz & 1))) break;
+      Level c;
+      c.g = f.g;
+      c.g.nx = (f.g.nx + 1) / 2;
+      c.g.ny = (f.g.ny + 1) / 2;
+      c.g.nz = (f.g.nz + 1) / 2;
+      c.g.pitch = nn4_row_pitch(c.g.nx, P->T);
+      for (int d = 0; d < 3; ++d) c.h[d] = 2.0 * f.h[d];
+      P->lv.push_back(c);
+    }
+  }
+  for (auto& L : P->lv) {
+    L.L = stencil_coef(L.h);
+    L.cfg = default_pass_cfg(P->T, P->vc && &L == &P->lv[0], L.g);
+    const size_t fb = field_bytes(L.g, P->T);
+    if ((rc = alloc(P, &L.r, fb)) || (rc = alloc(P, &L.e, fb)) || (rc = alloc(P, &L.t, fb))) {
+      destroy(P);
+      return rc;
+    }
+  }
+  const size_t fb64 = field_bytes(P->g64, NN4_F64);
+  if ((rc = alloc(P, (void**)&P->x64, fb64)) || (rc = alloc(P, (void**)&P->b64, fb64)) ||
+      (rc = alloc(P, (void**)&P->r64, fb64)) || (rc = alloc(P, (void**)&P->scal, 16 * sizeof(double)))) {
+    destroy(P);
+    return rc;
+  }
+  if (o.outer == NN4_OUTER_FCG) {
+    for (int t = 0; t < 2; ++t)
+      if ((rc = alloc(P, (void**)&P->p64[t], fb64)) || (rc = alloc(P, (void**)&P->q64[t], fb64))) {
+        destroy(P);
+        return rc;
+      }
+  }
+  if (P->vc) {
+    if ((rc = alloc(P, (void**)&P->k64, fb64)) ||
+        (rc = check_cuda(cudaMemcpy(P->k64, k, fb64, cudaMemcpyDeviceToDevice), "copy k")) ||
+        (rc = alloc(P, &P->lv[0].k, field_bytes(P->lv[0].g, P->T))) ||
+        (rc = launch_to_inner(P->T, P->k64, P->g64, P->lv[0].k, P->lv[0].g, 0))) {
+      destroy(P);
+      return rc;
+    }
+  }
+  // tensor maps
+  {
+    int bx, by;
+    pass_box(NN4_F64, P->cfg64, &bx, &by);
+    bool ok = make_tmap_3d(&P->tm_x64, NN4_F64, P->x64, g->n[0], g->n[1], g->n[2], g->pitch, bx, by);
+    if (P->vc) ok = ok && make_tmap_3d(&P->tm_k64, NN4_F64, P->k64, g->n[0], g->n[1], g->n[2], g->pitch, bx, by);
+    if (o.outer == NN4_OUTER_FCG)
+      for (int t = 0; t < 2; ++t)
+        ok = ok && make_tmap_3d(&P->tm_p64[t], NN4_F64, P->p64[t], g->n[0], g->n[1], g->n[2], g->pitch, bx, by);
+    if (!ok) {
+      destroy(P);
+      return set_error(NN4_ECUDA, "tensor map encode failed");
+    }
+    for (auto& L : P->lv)
+      if ((rc = make_level_maps(P, L))) {
+        destroy(P);
+        return rc;
+      }
+  }
+  // coarse operators and the coarsest inverse
+  std::vector<double> dense;
+  if (P->vc) {
+    rc = build_galerkin_hierarchy(P, dense);
+  } else {
+    Level& C = P->lv.back();
+    const int N = C.g.nx * C.g.ny * C.g.nz;
+    dense.assign((size_t)N * N, 0.0);
+    std::vector<double> x(N, 0.0), y(N);
+    for (int j = 0; j < N; ++j) {
+      x[j] = 1.0;
+      host_apply_const(C, x, y);
+      for (int i = 0; i < N; ++i) dense[(size_t)i * N + j] = y[i];
+      x[j] = 0.0;
+    }
+    rc = NN4_OK;
+  }
+  if (rc || (rc = build_coarsest(P, dense)) || (rc = check_cuda(cudaDeviceSynchronize(), "plan build"))) {
+    destroy(P);
+    return rc;
+  }
+  nn4_plan h = new nn4_plan_s;
+  h->impl = P;
+  *out = h;
+  return NN4_OK;
+}
+
+int nn4_plan_destroy(nn4_plan p) {
+  if (!p) return NN4_OK;
+  destroy(p->impl);
+  delete p;
+  return NN4_OK;
+}
+
+int nn4_vcycle(nn4_plan p, const void* b, void* x, void* stream) {
+  if (!p || !b || !x) return set_error(NN4_EINVAL, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(b) % 16 || reinterpret_cast<uintptr_t>(x) % 16)
+    return set_error(NN4_EINVAL, "arrays must be 16-byte aligned");
+  PlanImpl* P = p->impl;
+  Level& L0 = P->lv[0];
+  int bx, by;
+  pass_box(P->T, L0.cfg, &bx, &by);
+  CUtensorMap tm;
+  if (!make_tmap_3d(&tm, P->T, x, L0.g.nx, L0.g.ny, L0.g.nz, L0.g.pitch, bx, by))
+    return set_error(NN4_ECUDA, "tensor map encode failed");
+  Fine F{b, x, &tm};
+  return vcycle_impl(P, F, false, static_cast<cudaStream_t>(stream));
+}
+
+int nn4_pressure_solve(nn4_plan p, const double* b, double* x, double rtol, int32_t max_iters,
+                       nn4_solve_info* info, void* stream) {
+  if (!p || !b || !x) return set_error(NN4_EINVAL, "NULL argument");
+  PlanImpl* P = p->impl;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t fb = field_bytes(P->g64, NN4_F64);
+  int rc;
+  if ((rc = check_cuda(cudaMemcpyAsync(P->b64, b, fb, cudaMemcpyDeviceToDevice, s), "copy b")) ||
+      (rc = check_cuda(cudaMemcpyAsync(P->x64, x, fb, cudaMemcpyDeviceToDevice, s), "copy x")))
+    return rc;
+  const int st = solve_device(P, rtol, max_iters, info, s);
+  if (st != NN4_OK && st != NN4_ENOCONV) return st;
+  if ((rc = check_cuda(cudaMemcpyAsync(x, P->x64, fb, cudaMemcpyDeviceToDevice, s), "copy x out")) ||
+      (rc = check_cuda(cudaStreamSynchronize(s), "sync")))
+    return rc;
+  return st;
+}
+
+int nn4_pressure_solve_host(nn4_plan p, const double* b_host, double* x_host, double rtol, int32_t max_iters,
+                            nn4_solve_info* info, void* stream) {
+  if (!p || !b_host || !x_host) return set_error(NN4_EINVAL, "NULL argument");
+  PlanImpl* P = p->impl;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const LevelGeom& g = P->g64;
+  const size_t w = (size_t)g.nx * sizeof(double);
+  const size_t dp = (size_t)g.pitch * sizeof(double);
+  int rc;
+  if ((rc = check_cuda(cudaMemcpy2DAsync(P->b64, dp, b_host, w, w, (size_t)g.ny * g.nz, cudaMemcpyHostToDevice, s),
+                       "copy b in")) ||
+      (rc = check_cuda(cudaMemcpy2DAsync(P->x64, dp, x_host, w, w, (size_t)g.ny * g.nz, cudaMemcpyHostToDevice, s),
+                       "copy x in")))
+    return rc;
+  const int st = solve_device(P, rtol, max_iters, info, s);
+  if (st != NN4_OK && st != NN4_ENOCONV) return st;
+  if ((rc = check_cuda(cudaMemcpy2DAsync(x_host, w, P->x64, dp, w, (size_t)g.ny * g.nz, cudaMemcpyDeviceToHost, s),
+                       "copy x out")) ||
+      (rc = check_cuda(cudaStreamSynchronize(s), "sync")))
+    return rc;
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,327 @@
+// Q1 27-point stencil passes: apply, residual (+ FP64 norm) and weighted Jacobi, for the
+// constant-coefficient operator and for the variable-coefficient identity of Eq. k-T
+// (Section 2.2.4).
+//
+// Design (one kernel template for every pass):
+//   * a CTA owns an x-y tile of 32 x (TYT*RY) output nodes and marches along z over `zchunk`
+//     output planes; every input plane (with a one-node halo in x and y) is brought into shared
+//     memory by a 3D TMA tile load, `stages` planes in flight, each stage guarded by an mbarrier;
+//   * natural faces: the assembled boundary row equals the interior stencil on the field
+//     mirrored about the boundary node, scaled by w = prod_d (s_d / 2), s_d the number of
+//     elements next to the node along axis d.  Mirrored planes are fetched by mirrored TMA z
+//     coordinates; in-plane neighbours by mirrored shared-memory indices;
+//   * the interior stencil is sum-factorised by neighbour class: per input row the centre value
+//     r0 and the sum of the two x-neighbours r1; per plane p00 = r0, p10 = r1 and the y-neighbour
+//     sums p01, p11 of those; across planes the z-neighbour sums.  Output k then needs
+//     u(k-1) + v(k) + u(k+1) with u = sum c_ab1 p_ab and v = sum c_ab0 p_ab, kept as two running
+//     partial sums in registers (about 14 operations per node and field).
+#include "common.cuh"
+#include "internal.h"
+
+namespace nn4 {
+
+NN4_DEFINE_ERROR_ACCESSOR(stencil_error_word)
+
+namespace {
+
+template <typename T>
+constexpr int kAlign = 16 / (int)sizeof(T);  // TMA x coordinates must be multiples of this
+
+__device__ __forceinline__ float half_count(int i, int n) {
+  return 0.5f * (float)((i > 0) + (i < n - 1));
+}
+
+__device__ __forceinline__ bool on_dirichlet(const LevelGeom& g, int i, int j, int k) {
+  return (g.dir[0] && i == 0) || (g.dir[1] && i == g.nx - 1) || (g.dir[2] && j == 0) ||
+         (g.dir[3] && j == g.ny - 1) || (g.dir[4] && k == 0) || (g.dir[5] && k == g.nz - 1);
+}
+
+// Per-field running sums of one thread's RY outputs.
+template <typename A, int RY>
+struct Runner {
+  A p1[RY];  // partial of the output at the previous plane (u(p-1) + v(p))
+  A p2[RY];  // partial of the output at the current plane (u(p))
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < RY; ++r) p1[r] = p2[r] = A(0);
+  }
+};
+
+template <typename T, typename A, int RY, bool PROD>
+__device__ __forceinline__ void plane_uv(const T* __restrict__ sx, const T* __restrict__ sk,
+                                         const int* rowoff, int cc, int cl, int cr, const A* c,
+                                         A* u, A* v, A* centre) {
+  // Row sums r0 (centre) and r1 (x-neighbours) for the RY+2 rows the thread touches.
+  A r0[RY + 2], r1[RY + 2];
+#pragma unroll
+  for (int q = 0; q < RY + 2; ++q) {
+    const int o = rowoff[q];
+    if (PROD) {
+      r0[q] = to_acc(sx[o + cc]) * to_acc(sk[o + cc]);
+      r1[q] = to_acc(sx[o + cl]) * to_acc(sk[o + cl]) + to_acc(sx[o + cr]) * to_acc(sk[o + cr]);
+    } else {
+      r0[q] = to_acc(sx[o + cc]);
+      r1[q] = to_acc(sx[o + cl]) + to_acc(sx[o + cr]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RY; ++r) {
+    const A p00 = r0[r + 1], p10 = r1[r + 1];
+    const A p01 = r0[r] + r0[r + 2], p11 = r1[r] + r1[r + 2];
+    v[r] = c[0] * p00 + c[1] * p10 + c[2] * p01 + c[3] * p11;
+    u[r] = c[4] * p00 + c[5] * p10 + c[6] * p01 + c[7] * p11;
+    if (centre) centre[r] = p00;
+  }
+}
+
+template <typename T, int OP, bool VC, int RY, int TYT, int S>
+__global__ void __launch_bounds__(32 * TYT)
+    k_pass(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmk,
+           const PassArgs a) {
+  using A = typename Acc<T>::type;
+  constexpr int AL = kAlign<T>;
+  constexpr int BX = 32 + 2 * AL;
+  constexpr int BY = TYT * RY + 2;
+  constexpr int NF = VC ? 2 : 1;
+  constexpr int TILE_BYTES = BX * BY * (int)sizeof(T);
+  constexpr int TILE_PAD = (TILE_BYTES + 127) / 128 * 128;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * NF * TILE_PAD);
+  double* red = reinterpret_cast<double*>(bars + S);
+
+  const LevelGeom& g = a.g;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * (TYT * RY);
+  const int zs = blockIdx.z * a.zchunk;
+  const int ze = min(nz, zs + a.zchunk);
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  const int nplanes = ze - zs + 2;  // input planes zs-1 .. ze
+
+  if (tid == 0) {
+    prefetch_tmap(&tmx);
+    if (VC) prefetch_tmap(&tmk);
+#pragma unroll
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int q) {
+    const int s = q % S;
+    const int zp = mirror(zs - 1 + q, nz);
+    mbar_expect_tx(&bars[s], NF * TILE_BYTES);
+    tma_load_3d(smem + (s * NF) * TILE_PAD, &tmx, x0 - AL, y0 - 1, zp, &bars[s]);
+    if (VC) tma_load_3d(smem + (s * NF + 1) * TILE_PAD, &tmk, x0 - AL, y0 - 1, zp, &bars[s]);
+  };
+  if (tid == 0) {
+    for (int q = 0; q < min(S, nplanes); ++q) issue(q);
+  }
+
+  // Column indices in the tile (clamped so that idle lanes read valid shared memory).
+  const int i = x0 + threadIdx.x;
+  const int ic = min(i, nx - 1);
+  const int cc = ic - (x0 - AL);
+  const int cl = mirror(ic - 1, nx) - (x0 - AL);
+  const int cr = mirror(ic + 1, nx) - (x0 - AL);
+  const int jb = y0 + threadIdx.y * RY;
+  int rowoff[RY + 2];
+#pragma unroll
+  for (int q = 0; q < RY + 2; ++q) {
+    int jm = mirror(jb - 1 + q, ny);
+    jm = min(max(jm, y0 - 1), y0 + BY - 2);
+    rowoff[q] = (jm - (y0 - 1)) * BX;
+  }
+
+  A c[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) c[t] = (A)a.L.c[t];
+  const A wx = (A)half_count(ic, nx);
+
+  Runner<A, RY> sx, skx, sk;  // L~x, L~(kx), L~k
+  sx.zero();
+  if (VC) {
+    skx.zero();
+    sk.zero();
+  }
+  A xc1[RY], kc1[RY];  // centre values of the previous input plane (the pending output)
+  double nrm = 0.0, dt2 = 0.0;
+  bool failed = false;
+
+  for (int q = 0; q < nplanes; ++q) {
+    const int s = q % S;
+    if (!mbar_wait_bounded(&bars[s], (uint32_t)((q / S) & 1))) failed = true;
+    const T* tx_ = reinterpret_cast<const T*>(smem + (s * NF) * TILE_PAD);
+    const T* tk_ = reinterpret_cast<const T*>(smem + (s * NF + 1) * TILE_PAD);
+    A ux[RY], vx[RY], xcn[RY];
+    plane_uv<T, A, RY, false>(tx_, tx_, rowoff, cc, cl, cr, c, ux, vx, xcn);
+    A ukx[RY], vkx[RY], uk[RY], vk[RY], kcn[RY];
+    if (VC) {
+      plane_uv<T, A, RY, true>(tx_, tk_, rowoff, cc, cl, cr, c, ukx, vkx, nullptr);
+      plane_uv<T, A, RY, false>(tk_, tk_, rowoff, cc, cl, cr, c, uk, vk, kcn);
+    }
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    if (tid == 0 && q + S < nplanes) issue(q + S);
+
+    const int kout = zs + q - 2;  // output plane completed by this input plane
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      if (q >= 2) {
+        const int j = jb + r;
+        if (i < nx && j < ny) {
+          const A w = wx * (A)half_count(j, ny) * (A)half_count(kout, nz);
+          const A Lx = sx.p1[r] + ux[r];
+          A Ax, D;
+          if (VC) {
+            const A Lkx = skx.p1[r] + ukx[r];
+            const A Lk = sk.p1[r] + uk[r];
+            Ax = (A)0.5 * w * (Lkx + kc1[r] * Lx - xc1[r] * Lk);
+            D = w * (c[0] * kc1[r] - (A)0.5 * Lk);
+          } else {
+            Ax = w * Lx;
+            D = w * c[0];
+          }
+          const long long idx = (long long)i + g.pitch * ((long long)j + (long long)ny * kout);
+          T* out = reinterpret_cast<T*>(a.out);
+          if (OP == OP_APPLY) {
+            out[idx] = from_acc<T>(Ax);
+          } else {
+            const bool dirn = on_dirichlet(g, i, j, kout);
+            const A bv = to_acc(reinterpret_cast<const T*>(a.b)[idx]);
+            if (OP == OP_RESIDUAL) {
+              const A rv = dirn ? A(0) : bv - Ax;
+              out[idx] = from_acc<T>(rv);
+              nrm += (double)rv * (double)rv;
+            } else if (OP == OP_MATVEC) {
+              const A qv = dirn ? A(0) : Ax;
+              out[idx] = from_acc<T>(qv);
+              nrm += (double)xc1[r] * (double)qv;
+              dt2 += (double)xc1[r] * (double)bv;
+            } else {
+              const A xn = dirn ? xc1[r] : xc1[r] + (A)a.omega * (bv - Ax) / D;
+              out[idx] = from_acc<T>(xn);
+            }
+          }
+        }
+      }
+      // shift the running sums: the output of this plane still needs u of the next plane
+      sx.p1[r] = sx.p2[r] + vx[r];
+      sx.p2[r] = ux[r];
+      xc1[r] = xcn[r];
+      if (VC) {
+        skx.p1[r] = skx.p2[r] + vkx[r];
+        skx.p2[r] = ukx[r];
+        sk.p1[r] = sk.p2[r] + vk[r];
+        sk.p2[r] = uk[r];
+        kc1[r] = kcn[r];
+      }
+    }
+  }
+  if (failed) {
+    // drain copies that may still be in flight before the CTA exits
+    if (tid == 0) {
+      for (int q = 0; q < min(S, nplanes); ++q) mbar_wait_bounded(&bars[q], 0u);
+    }
+    __syncthreads();
+    return;
+  }
+  if ((OP == OP_RESIDUAL || OP == OP_MATVEC) && a.norm2 != nullptr) block_sum_atomic(nrm, a.norm2, red);
+  if (OP == OP_MATVEC && a.dot2 != nullptr) block_sum_atomic(dt2, a.dot2, red);
+}
+
+template <typename T, int OP, bool VC, int RY, int TYT, int S>
+int launch_t(const PassArgs& a, const CUtensorMap& mx, const CUtensorMap& mk, cudaStream_t st) {
+  constexpr int AL = kAlign<T>;
+  constexpr int BX = 32 + 2 * AL;
+  constexpr int BY = TYT * RY + 2;
+  constexpr int NF = VC ? 2 : 1;
+  constexpr int TILE_PAD = (BX * BY * (int)sizeof(T) + 127) / 128 * 128;
+  const size_t smem = (size_t)S * NF * TILE_PAD + S * 8 + 32 * 8;
+  auto kern = k_pass<T, OP, VC, RY, TYT, S>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(stencil pass)");
+  }
+  dim3 grid((a.g.nx + 31) / 32, (a.g.ny + TYT * RY - 1) / (TYT * RY), (a.g.nz + a.zchunk - 1) / a.zchunk);
+  kern<<<grid, dim3(32, TYT), smem, st>>>(mx, mk, a);
+  return check_cuda(cudaGetLastError(), "stencil pass launch");
+}
+
+template <typename T, int OP, bool VC>
+int dispatch_cfg(const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx,
+                 const CUtensorMap& mk, cudaStream_t st) {
+  // The configurations the autotuner chooses from.
+  if (cfg.stages == 3 && cfg.tyt == 4 && cfg.ry == 4) return launch_t<T, OP, VC, 4, 4, 3>(a, mx, mk, st);
+  if (cfg.stages == 3 && cfg.tyt == 8 && cfg.ry == 2) return launch_t<T, OP, VC, 2, 8, 3>(a, mx, mk, st);
+  if (cfg.stages == 3 && cfg.tyt == 4 && cfg.ry == 2) return launch_t<T, OP, VC, 2, 4, 3>(a, mx, mk, st);
+  if (cfg.stages == 4 && cfg.tyt == 4 && cfg.ry == 4) return launch_t<T, OP, VC, 4, 4, 4>(a, mx, mk, st);
+  if (cfg.stages == 2 && cfg.tyt == 2 && cfg.ry == 2) return launch_t<T, OP, VC, 2, 2, 2>(a, mx, mk, st);
+  return set_error(NN4_EINVAL, "unsupported stencil pass configuration");
+}
+
+template <typename T>
+int dispatch_op(int op, bool vc, const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx,
+                const CUtensorMap& mk, cudaStream_t st) {
+  switch (op * 2 + (vc ? 1 : 0)) {
+    case OP_APPLY * 2: return dispatch_cfg<T, OP_APPLY, false>(a, cfg, mx, mk, st);
+    case OP_APPLY * 2 + 1: return dispatch_cfg<T, OP_APPLY, true>(a, cfg, mx, mk, st);
+    case OP_RESIDUAL * 2: return dispatch_cfg<T, OP_RESIDUAL, false>(a, cfg, mx, mk, st);
+    case OP_RESIDUAL * 2 + 1: return dispatch_cfg<T, OP_RESIDUAL, true>(a, cfg, mx, mk, st);
+    case OP_JACOBI * 2: return dispatch_cfg<T, OP_JACOBI, false>(a, cfg, mx, mk, st);
+    case OP_JACOBI * 2 + 1: return dispatch_cfg<T, OP_JACOBI, true>(a, cfg, mx, mk, st);
+    case OP_MATVEC * 2: return dispatch_cfg<T, OP_MATVEC, false>(a, cfg, mx, mk, st);
+    case OP_MATVEC * 2 + 1: return dispatch_cfg<T, OP_MATVEC, true>(a, cfg, mx, mk, st);
+  }
+  return set_error(NN4_EINVAL, "bad stencil op");
+}
+
+}  // namespace
+
+PassCfg default_pass_cfg(nn4_dtype dt, bool vc, const LevelGeom& g) {
+  PassCfg c;
+  c.ry = (dt == NN4_F64 && vc) ? 2 : 4;
+  c.tyt = (dt == NN4_F64 && vc) ? 8 : 4;
+  c.stages = 3;
+  const int tiles = ((g.nx + 31) / 32) * ((g.ny + c.tyt * c.ry - 1) / (c.tyt * c.ry));
+  // aim at >= ~1200 CTAs (8 per SM) but keep at least 8 output planes per CTA
+  int zc = g.nz;
+  while (zc > 8 && tiles * ((g.nz + zc - 1) / zc) < 1216) zc = (zc + 1) / 2;
+  c.zchunk = zc;
+  return c;
+}
+
+int pass_box(nn4_dtype dt, const PassCfg& cfg, int* box_x, int* box_y) {
+  const int al = 16 / (int)dtype_size(dt);
+  *box_x = 32 + 2 * al;
+  *box_y = cfg.tyt * cfg.ry + 2;
+  return NN4_OK;
+}
+
+int launch_pass(nn4_dtype dt, int op, const PassArgs& a, const void* x, const void* k,
+                const PassCfg& cfg, cudaStream_t s, const CUtensorMap* mx, const CUtensorMap* mk) {
+  CUtensorMap tx, tk;
+  int bx, by;
+  pass_box(dt, cfg, &bx, &by);
+  if (!mx) {
+    if (!make_tmap_3d(&tx, dt, x, a.g.nx, a.g.ny, a.g.nz, a.g.pitch, bx, by))
+      return set_error(NN4_ECUDA, "cuTensorMapEncodeTiled failed for x");
+    mx = &tx;
+  }
+  const bool vc = (k != nullptr) || (mk != nullptr);
+  if (vc && !mk) {
+    if (!make_tmap_3d(&tk, dt, k, a.g.nx, a.g.ny, a.g.nz, a.g.pitch, bx, by))
+      return set_error(NN4_ECUDA, "cuTensorMapEncodeTiled failed for k");
+    mk = &tk;
+  }
+  if (!vc) mk = mx;
+  switch (dt) {
+    case NN4_F64: return dispatch_op<double>(op, vc, a, cfg, *mx, *mk, s);
+    case NN4_F32: return dispatch_op<float>(op, vc, a, cfg, *mx, *mk, s);
+    case NN4_BF16: return dispatch_op<bf16>(op, vc, a, cfg, *mx, *mk, s);
+  }
+  return set_error(NN4_EINVAL, "bad dtype");
+}
+
+}  // namespace nn4

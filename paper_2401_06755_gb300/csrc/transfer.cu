@@ -1,0 +1,135 @@
+// Inter-grid transfers of the sawtooth multigrid (Section 2.4): stride-2 restriction R = P^T and
+// trilinear prolongation P between a fine vertex grid and the grid of its even-indexed nodes.
+#include "common.cuh"
+#include "internal.h"
+
+namespace nn4 {
+namespace {
+
+__device__ __forceinline__ bool dir_node(const LevelGeom& g, int i, int j, int k) {
+  return (g.dir[0] && i == 0) || (g.dir[1] && i == g.nx - 1) || (g.dir[2] && j == 0) ||
+         (g.dir[3] && j == g.ny - 1) || (g.dir[4] && k == 0) || (g.dir[5] && k == g.nz - 1);
+}
+
+// One thread per coarse node: r_c(I) = sum_{d in {-1,0,1}^3} prod_d (1/2)^|d| r_f(2I + d) over
+// the fine nodes that exist; zero at coarse Dirichlet nodes.  Separable: x, then y, then z.
+template <typename T>
+__global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ rc, const LevelGeom gf,
+                           const LevelGeom gc) {
+  using A = typename Acc<T>::type;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= gc.nx || J >= gc.ny) return;
+  A acc = A(0);
+  if (!dir_node(gc, I, J, K)) {
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int k = 2 * K + dz;
+      if (k < 0 || k >= gf.nz) continue;
+      A az = A(0);
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int j = 2 * J + dy;
+        if (j < 0 || j >= gf.ny) continue;
+        const T* row = rf + gf.pitch * ((long long)j + (long long)gf.ny * k);
+        const int i = 2 * I;
+        A ax = to_acc(row[i]);
+        if (i > 0) ax += A(0.5) * to_acc(row[i - 1]);
+        if (i + 1 < gf.nx) ax += A(0.5) * to_acc(row[i + 1]);
+        az += (dy == 0 ? A(1) : A(0.5)) * ax;
+      }
+      acc += (dz == 0 ? A(1) : A(0.5)) * az;
+    }
+  }
+  rc[I + gc.pitch * ((long long)J + (long long)gc.ny * K)] = from_acc<T>(acc);
+}
+
+// One thread per fine node: e_f(i) (+)= sum over the coarse nodes bracketing i of
+// prod_d (1 at an even index, 1/2 for each of the two parents at an odd index) e_c.
+template <typename T>
+__global__ void k_prolong(const T* __restrict__ ec, T* ef, const T* base, const LevelGeom gc,
+                          const LevelGeom gf) {
+  using A = typename Acc<T>::type;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= gf.nx || j >= gf.ny) return;
+  const long long idx = i + gf.pitch * ((long long)j + (long long)gf.ny * k);
+  if (dir_node(gf, i, j, k)) {
+    ef[idx] = base ? base[idx] : from_acc<T>(A(0));
+    return;
+  }
+  const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+  const int I1 = I0 + (i & 1), J1 = J0 + (j & 1), K1 = K0 + (k & 1);
+  const A wx = (i & 1) ? A(0.5) : A(1), wy = (j & 1) ? A(0.5) : A(1), wz = (k & 1) ? A(0.5) : A(1);
+  auto at = [&](int I, int J, int K) {
+    return to_acc(ec[I + gc.pitch * ((long long)J + (long long)gc.ny * K)]);
+  };
+  A v = at(I0, J0, K0);
+  if (i & 1) v += at(I1, J0, K0);
+  if (j & 1) {
+    A t = at(I0, J1, K0);
+    if (i & 1) t += at(I1, J1, K0);
+    v += t;
+  }
+  if (k & 1) {
+    A t = at(I0, J0, K1);
+    if (i & 1) t += at(I1, J0, K1);
+    if (j & 1) {
+      A t2 = at(I0, J1, K1);
+      if (i & 1) t2 += at(I1, J1, K1);
+      t += t2;
+    }
+    v += t;
+  }
+  v *= wx * wy * wz;
+  if (base) v += to_acc(base[idx]);
+  ef[idx] = from_acc<T>(v);
+}
+
+template <typename T>
+int restrict_t(const void* rf, const LevelGeom& gf, void* rc, const LevelGeom& gc, cudaStream_t s) {
+  dim3 blk(32, 4);
+  dim3 grd((gc.nx + 31) / 32, (gc.ny + 3) / 4, gc.nz);
+  k_restrict<T><<<grd, blk, 0, s>>>(static_cast<const T*>(rf), static_cast<T*>(rc), gf, gc);
+  return check_cuda(cudaGetLastError(), "restrict launch");
+}
+
+template <typename T>
+int prolong_t(const void* ec, const LevelGeom& gc, void* ef, const void* base, const LevelGeom& gf,
+              cudaStream_t s) {
+  dim3 blk(32, 4);
+  dim3 grd((gf.nx + 31) / 32, (gf.ny + 3) / 4, gf.nz);
+  k_prolong<T><<<grd, blk, 0, s>>>(static_cast<const T*>(ec), static_cast<T*>(ef), static_cast<const T*>(base), gc, gf);
+  return check_cuda(cudaGetLastError(), "prolong launch");
+}
+
+}  // namespace
+
+int launch_restrict(nn4_dtype dt, const void* rf, const LevelGeom& gf, void* rc,
+                    const LevelGeom& gc, cudaStream_t s) {
+  switch (dt) {
+    case NN4_F64: return restrict_t<double>(rf, gf, rc, gc, s);
+    case NN4_F32: return restrict_t<float>(rf, gf, rc, gc, s);
+    case NN4_BF16: return restrict_t<bf16>(rf, gf, rc, gc, s);
+  }
+  return set_error(NN4_EINVAL, "bad dtype");
+}
+
+int launch_prolong_base(nn4_dtype dt, const void* ec, const LevelGeom& gc, void* ef, const void* base,
+                        const LevelGeom& gf, cudaStream_t s) {
+  switch (dt) {
+    case NN4_F64: return prolong_t<double>(ec, gc, ef, base, gf, s);
+    case NN4_F32: return prolong_t<float>(ec, gc, ef, base, gf, s);
+    case NN4_BF16: return prolong_t<bf16>(ec, gc, ef, base, gf, s);
+  }
+  return set_error(NN4_EINVAL, "bad dtype");
+}
+
+int launch_prolong(nn4_dtype dt, const void* ec, const LevelGeom& gc, void* ef,
+                   const LevelGeom& gf, int accumulate, cudaStream_t s) {
+  return launch_prolong_base(dt, ec, gc, ef, accumulate ? ef : nullptr, gf, s);
+}
+
+}  // namespace nn4

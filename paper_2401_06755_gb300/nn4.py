@@ -1,0 +1,255 @@
+"""Python binding of the C ABI in include/nn4.h (argument marshalling only).
+
+Every function here forwards to ``_lib/libnn4.so``; no step of the method runs in Python.  If the
+library is missing the import of a function raises: there is no fallback path.
+
+Fields are torch tensors of shape (nz, ny, pitch) ("storage") whose first nx entries of every row
+hold the nodes; :func:`field` allocates one with the library's pitch, and :func:`nodes` returns
+the (nz, ny, nx) view.  PyTorch provides device memory and streams only.
+"""
+
+import ctypes
+import os
+from dataclasses import dataclass, field as dc_field
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libnn4.so")
+
+OK, EINVAL, ECUDA, ENOMEM, ENOCONV, ENONFINITE, ETIMEOUT, EBOUNDS, EUNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+F64, F32, BF16 = 0, 1, 2
+DIRICHLET, NATURAL = 0, 1
+OUTER_CYCLES, OUTER_FCG = 0, 1
+
+_TORCH = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16}
+_CODE = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
+
+
+class NN4Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nn4 status {code}: {msg}")
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("h", ctypes.c_double * 3), ("bc", ctypes.c_int32 * 6),
+                ("pitch", ctypes.c_int64)]
+
+
+class _PlanOpts(ctypes.Structure):
+    _fields_ = [("inner", ctypes.c_int), ("inner_cycles", ctypes.c_int32), ("outer", ctypes.c_int32),
+                ("omega", ctypes.c_double), ("use_graph", ctypes.c_int32),
+                ("check_every", ctypes.c_int32)]
+
+
+class _SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("cycles", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libnn4.so (raising if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "python -m paper_2401_06755_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+        G = ctypes.POINTER(_Grid)
+        sig = {
+            "nn4_row_pitch": (ctypes.c_int64, [i32, ctypes.c_int]),
+            "nn4_stencil_apply": (ctypes.c_int, [G, ctypes.c_int, vp, vp, vp, vp]),
+            "nn4_residual": (ctypes.c_int, [G, ctypes.c_int, vp, vp, vp, vp, vp, vp]),
+            "nn4_restrict": (ctypes.c_int, [G, ctypes.c_int, vp, vp, vp]),
+            "nn4_prolong": (ctypes.c_int, [G, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
+            "nn4_jacobi_smooth": (ctypes.c_int, [G, ctypes.c_int, vp, vp, vp, vp, dbl, vp]),
+            "nn4_plan_opts_default": (None, [ctypes.POINTER(_PlanOpts)]),
+            "nn4_plan_create": (ctypes.c_int, [G, vp, ctypes.POINTER(_PlanOpts), ctypes.POINTER(vp)]),
+            "nn4_plan_destroy": (ctypes.c_int, [vp]),
+            "nn4_vcycle": (ctypes.c_int, [vp, vp, vp, vp]),
+            "nn4_pressure_solve": (ctypes.c_int, [vp, vp, vp, dbl, i32, ctypes.POINTER(_SolveInfo), vp]),
+            "nn4_pressure_solve_host": (ctypes.c_int, [vp, vp, vp, dbl, i32, ctypes.POINTER(_SolveInfo), vp]),
+            "nn4_last_error": (ctypes.c_char_p, []),
+            "nn4_device_error": (ctypes.c_int, []),
+            "nn4_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != OK:
+        raise NN4Error(code, lib().nn4_last_error().decode())
+    return code
+
+
+@dataclass
+class Grid:
+    """Vertex grid: n = (nx, ny, nz) nodes, spacing h, one of DIRICHLET / NATURAL per face."""
+    n: tuple
+    h: tuple
+    bc: tuple = dc_field(default_factory=lambda: (NATURAL,) * 6)
+
+    def pitch(self, dtype):
+        return row_pitch(self.n[0], dtype)
+
+    def c(self, dtype):
+        g = _Grid()
+        g.n[:] = list(self.n)
+        g.h[:] = [float(v) for v in self.h]
+        g.bc[:] = list(self.bc)
+        g.pitch = self.pitch(dtype)
+        return g
+
+    def coarse(self):
+        return Grid(tuple((m + 1) // 2 for m in self.n), tuple(2.0 * v for v in self.h), self.bc)
+
+
+def row_pitch(nx, dtype):
+    code = dtype if isinstance(dtype, int) else _CODE[dtype]
+    return int(lib().nn4_row_pitch(int(nx), code))
+
+
+def field(grid, dtype=torch.float64, device="cuda", fill=0.0):
+    """A zero (or ``fill``) pitched storage tensor (nz, ny, pitch) for ``grid``."""
+    nx, ny, nz = grid.n
+    return torch.full((nz, ny, row_pitch(nx, dtype)), fill, dtype=dtype, device=device)
+
+
+def nodes(storage, grid):
+    """The (nz, ny, nx) view of the node values of a storage tensor."""
+    return storage[:, :, :grid.n[0]]
+
+
+def to_field(a, grid, dtype=torch.float64, device="cuda"):
+    """Copies an (nz, ny, nx) array into a new pitched storage tensor."""
+    f = field(grid, dtype, device)
+    nodes(f, grid).copy_(torch.as_tensor(a).to(dtype))
+    return f
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dt(t):
+    return _CODE[t.dtype]
+
+
+def stencil_apply(grid, x, k=None, y=None, stream=None):
+    y = torch.empty_like(x) if y is None else y
+    g = grid.c(x.dtype)
+    _check(lib().nn4_stencil_apply(ctypes.byref(g), _dt(x), _ptr(x), _ptr(k), _ptr(y), _stream(stream)))
+    return y
+
+
+def residual(grid, b, x, k=None, r=None, norm2=None, stream=None):
+    r = torch.empty_like(x) if r is None else r
+    g = grid.c(x.dtype)
+    _check(lib().nn4_residual(ctypes.byref(g), _dt(x), _ptr(b), _ptr(x), _ptr(k), _ptr(r), _ptr(norm2),
+                              _stream(stream)))
+    return r
+
+
+def restrict(grid, r_fine, r_coarse=None, stream=None):
+    if r_coarse is None:
+        r_coarse = field(grid.coarse(), r_fine.dtype, r_fine.device)
+    g = grid.c(r_fine.dtype)
+    _check(lib().nn4_restrict(ctypes.byref(g), _dt(r_fine), _ptr(r_fine), _ptr(r_coarse), _stream(stream)))
+    return r_coarse
+
+
+def prolong(grid, e_coarse, e_fine=None, accumulate=False, stream=None):
+    if e_fine is None:
+        e_fine = field(grid, e_coarse.dtype, e_coarse.device)
+    g = grid.c(e_coarse.dtype)
+    _check(lib().nn4_prolong(ctypes.byref(g), _dt(e_coarse), _ptr(e_coarse), _ptr(e_fine),
+                             int(bool(accumulate)), _stream(stream)))
+    return e_fine
+
+
+def jacobi_smooth(grid, b, x_in, k=None, x_out=None, omega=2.0 / 3.0, stream=None):
+    x_out = torch.empty_like(x_in) if x_out is None else x_out
+    g = grid.c(x_in.dtype)
+    _check(lib().nn4_jacobi_smooth(ctypes.byref(g), _dt(x_in), _ptr(b), _ptr(k), _ptr(x_in), _ptr(x_out),
+                                   float(omega), _stream(stream)))
+    return x_out
+
+
+def device_error():
+    return lib().nn4_device_error()
+
+
+def version():
+    return lib().nn4_version().decode()
+
+
+class Plan:
+    """Multigrid hierarchy for one grid (and optional FP64 coefficient field k)."""
+
+    def __init__(self, grid, k=None, inner=F64, inner_cycles=1, outer=OUTER_CYCLES, omega=2.0 / 3.0,
+                 use_graph=True, check_every=1):
+        o = _PlanOpts()
+        lib().nn4_plan_opts_default(ctypes.byref(o))
+        o.inner, o.inner_cycles, o.outer = int(inner), int(inner_cycles), int(outer)
+        o.omega, o.use_graph, o.check_every = float(omega), int(bool(use_graph)), int(check_every)
+        self.grid = grid
+        self.inner = inner
+        self._k = k  # keep the coefficient alive while the plan exists
+        self._g = grid.c(torch.float64)
+        h = ctypes.c_void_p(0)
+        _check(lib().nn4_plan_create(ctypes.byref(self._g), _ptr(k), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().nn4_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vcycle(self, b, x, stream=None):
+        _check(lib().nn4_vcycle(self._h, _ptr(b), _ptr(x), _stream(stream)))
+        return x
+
+    def _solve(self, fn, b, x, rtol, max_iters, history_len, stream, ptr):
+        hist = (ctypes.c_double * max(1, history_len))()
+        info = _SolveInfo()
+        info.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+        info.history_len = history_len
+        code = fn(self._h, ptr(b), ptr(x), float(rtol), int(max_iters), ctypes.byref(info), _stream(stream))
+        if code not in (OK, ENOCONV):
+            _check(code)
+        n = min(history_len, info.iterations + 1)
+        return {"status": code, "iterations": info.iterations, "cycles": info.cycles,
+                "rel_res": info.rel_res, "history": list(hist[:n])}
+
+    def solve(self, b, x, rtol=1e-8, max_iters=200, history_len=512, stream=None):
+        """Pressure solve on device FP64 storage tensors b, x (x: initial guess, then solution)."""
+        return self._solve(lib().nn4_pressure_solve, b, x, rtol, max_iters, history_len, stream, _ptr)
+
+    def solve_host(self, b, x, rtol=1e-8, max_iters=200, history_len=512, stream=None):
+        """The same with dense (nz, ny, nx) host FP64 tensors (pinned for full copy speed)."""
+        assert b.device.type == "cpu" and x.device.type == "cpu" and b.is_contiguous() and x.is_contiguous()
+        return self._solve(lib().nn4_pressure_solve_host, b, x, rtol, max_iters, history_len, stream,
+                           lambda t: ctypes.c_void_p(t.data_ptr()))
