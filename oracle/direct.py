@@ -16,7 +16,7 @@ def solve_dense(g, b, k=None):
     A, free = mg.dense_matrix(g, k)
     rhs = b.ravel()[free]
     if mg.is_singular(g):
-        sol = np.linalg.lstsq(A, rhs, rcond=None)[0]
+        sol = mg.min_norm_solve(A, rhs)
     else:
         sol = np.linalg.solve(A, rhs)
     x = np.zeros(int(np.prod(g.shape)))

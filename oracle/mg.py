@@ -186,13 +186,22 @@ def coarse_solve(g, r, k=None):
     """Exact solve A e = r on the coarsest grid; minimum-norm (zero-mean) when singular."""
     A, free = dense_matrix(g, k)
     rhs = r.ravel()[free]
-    if is_singular(g):
-        sol = np.linalg.pinv(A) @ rhs
-    else:
-        sol = np.linalg.solve(A, rhs)
+    sol = min_norm_solve(A, rhs) if is_singular(g) else np.linalg.solve(A, rhs)
     e = np.zeros(int(np.prod(g.shape)))
     e[free] = sol
     return e.reshape(g.shape)
+
+
+def min_norm_solve(A, rhs):
+    """Minimum-norm solution of a singular symmetric system (null space: the constants).
+
+    Eigen-decomposition with a numerical-rank cutoff of 1e-10 relative to the largest
+    eigenvalue: the exact null eigenvalue is computed at rounding level, and an SVD cutoff at
+    machine precision would keep it and add a large spurious constant.
+    """
+    w, V = np.linalg.eigh(0.5 * (A + A.T))
+    keep = np.abs(w) > 1e-10 * np.abs(w).max()
+    return V[:, keep] @ ((V[:, keep].T @ rhs) / w[keep])
 
 
 # ---------------------------------------------------------------- cycle and solve
@@ -298,7 +307,7 @@ class Levels:
         free = np.flatnonzero(~dirichlet_mask(g).ravel())
         A = self.A[l].toarray()[np.ix_(free, free)]
         rhs = r.ravel()[free]
-        sol = np.linalg.pinv(A) @ rhs if is_singular(g) else np.linalg.solve(A, rhs)
+        sol = min_norm_solve(A, rhs) if is_singular(g) else np.linalg.solve(A, rhs)
         e = np.zeros(int(np.prod(g.shape)))
         e[free] = sol
         return e.reshape(g.shape)

@@ -192,3 +192,17 @@ def test_fcg_sphere_33_converges_fast():
     assert hist[-1] <= 1e-8 and len(hist) - 1 <= 40
     _, hist_plain = mg.pressure_solve(g, b, k=k, fixed_cycles=12)
     assert hist_plain[-1] > 1e-6
+
+
+def test_min_norm_coarsest_solve_high_contrast():
+    """The singular coarsest solve returns the zero-mean solution even when the null
+    eigenvalue is at rounding level (1000:1 sphere, Galerkin 3^3 level)."""
+    n = 17
+    g = mg.Grid((n,) * 3, (1 / 16,) * 3)
+    lv = mg.Levels(g, _sphere_k(g))
+    A = lv.A[-1].toarray()
+    r = np.random.default_rng(0).standard_normal(A.shape[0])
+    r -= r.mean()
+    e = mg.min_norm_solve(A, r)
+    assert abs(e.mean()) < 1e-10 * np.abs(e).max()
+    np.testing.assert_allclose(A @ e, r, atol=1e-9 * np.abs(r).max())
