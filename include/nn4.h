@@ -117,9 +117,12 @@ typedef struct {
   double omega;          /* Jacobi weight, 2/3 in the paper's setting */
   int32_t use_graph;     /* capture each outer iteration as a CUDA graph (1) or launch eagerly */
   int32_t check_every;   /* read the residual norm back every this many outer iterations (>=1) */
+  int32_t profile;       /* 1: launch eagerly and time every kernel with CUDA events (see
+                            nn4_plan_profile); for measurement only */
 } nn4_plan_opts;
 
-/* Fills o with the defaults: F64, 1 cycle, NN4_OUTER_CYCLES, omega 2/3, graphs on, check 1. */
+/* Fills o with the defaults: F64, 1 cycle, NN4_OUTER_CYCLES, omega 2/3, graphs on, check 1,
+ * profile off. */
 void nn4_plan_opts_default(nn4_plan_opts* o);
 
 typedef struct nn4_plan_s* nn4_plan;
@@ -148,6 +151,7 @@ typedef struct {
   double* history;       /* caller-owned host array or NULL: relative residual after each
                             outer iteration, history[0] for the initial x */
   int32_t history_len;   /* capacity of history */
+  int64_t kernels;       /* kernels launched by the call (graph kernel nodes included) */
 } nn4_solve_info;
 
 /* Solves A x = b (FP64 device arrays on the plan's grid, pitch g->pitch) from the x given,
@@ -163,6 +167,28 @@ int nn4_pressure_solve(nn4_plan p, const double* b, double* x, double rtol, int3
  * through plan-owned device buffers inside the call. */
 int nn4_pressure_solve_host(nn4_plan p, const double* b_host, double* x_host, double rtol,
                             int32_t max_iters, nn4_solve_info* info, void* stream);
+
+/* Per-kernel timing of a plan created with profile = 1: for every kernel category launched since
+ * the last call (or plan creation), its name, launch count and summed device time in ms, taken
+ * from CUDA events recorded on the launching stream around each launch.  Writes up to `cap`
+ * entries and returns how many categories exist (or a negative status).  Synchronises. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} nn4_kernel_time;
+
+int nn4_plan_profile(nn4_plan p, nn4_kernel_time* out, int32_t cap);
+
+/* Static facts of a plan: number of levels and node counts per level (up to 16). */
+typedef struct {
+  int32_t levels;
+  int32_t n[16][3];
+  int32_t coarsest_free;
+  int64_t device_bytes;  /* device memory owned by the plan */
+} nn4_plan_info;
+
+int nn4_plan_query(nn4_plan p, nn4_plan_info* out);
 
 /* ----------------------------------------------------------------- diagnostics */
 

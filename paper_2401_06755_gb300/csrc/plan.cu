@@ -63,8 +63,17 @@ struct PlanImpl {
   int hist_cap = 0;
   double* host_hist = nullptr;  // pinned
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int64_t graph_kernels[2] = {0, 0};
   cudaStream_t graph_stream = nullptr;
   std::vector<void*> allocs;
+  size_t device_bytes = 0;
+  // launch accounting and optional per-kernel event timing
+  int64_t kernels = 0;
+  struct Rec {
+    std::string name;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<Rec> recs;
 };
 
 namespace {
@@ -73,11 +82,38 @@ int alloc(PlanImpl* P, void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) return check_cuda(e, "cudaMalloc (plan)");
   P->allocs.push_back(*p);
+  P->device_bytes += bytes;
   return check_cuda(cudaMemset(*p, 0, bytes), "cudaMemset (plan)");
 }
 
 size_t field_bytes(const LevelGeom& g, nn4_dtype dt) {
   return (size_t)g.pitch * g.ny * g.nz * dtype_size(dt);
+}
+
+// Every kernel launch of the plan goes through K(): it counts the launch and, in profile mode,
+// brackets it with CUDA events on the launching stream.
+template <typename F>
+int K(PlanImpl* P, const std::string& name, cudaStream_t s, F&& launch) {
+  PlanImpl::Rec r;
+  const bool prof = P->o.profile != 0;
+  if (prof) {
+    r.name = name;
+    cudaEventCreate(&r.e0);
+    cudaEventCreate(&r.e1);
+    cudaEventRecord(r.e0, s);
+  }
+  const int rc = launch();
+  P->kernels += 1;
+  if (prof) {
+    cudaEventRecord(r.e1, s);
+    P->recs.push_back(r);
+  }
+  return rc;
+}
+
+std::string lvl(int l) { return l >= 3 ? std::string("L3+") : "L" + std::to_string(l); }
+const char* opname(int op) {
+  return op == OP_APPLY ? "apply" : op == OP_RESIDUAL ? "residual" : op == OP_JACOBI ? "jacobi" : "matvec";
 }
 
 // ---------------------------------------------------------------- host dense algebra
@@ -275,9 +311,13 @@ int run_pass(PlanImpl* P, int l, int op, const void* x, const CUtensorMap* mx, c
   a.out = out;
   a.norm2 = norm2;
   a.zchunk = L.cfg.zchunk;
-  if (P->vc && l > 0) return launch_pass27(P->T, op, a, x, L.a27, s);
+  if (P->vc && l > 0)
+    return K(P, std::string("pass27:") + opname(op) + ":" + lvl(l), s,
+             [&] { return launch_pass27(P->T, op, a, x, L.a27, s); });
   const bool vc0 = P->vc && l == 0;
-  return launch_pass(P->T, op, a, x, vc0 ? L.k : nullptr, L.cfg, s, mx, vc0 ? &L.tm_k : nullptr);
+  return K(P, std::string("pass:") + opname(op) + ":" + lvl(l), s, [&] {
+    return launch_pass(P->T, op, a, x, vc0 ? L.k : nullptr, L.cfg, s, mx, vc0 ? &L.tm_k : nullptr);
+  });
 }
 
 int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
@@ -286,9 +326,10 @@ int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
   int rc;
   Level& L0 = P->lv[0];
   if (nl == 1) {  // the fine grid is the coarsest: e += A^-1 (r - A e)
-    if (first) return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, F.r, F.e, L0.g, 0, s);
+    if (first)
+      return K(P, "coarsest", s, [&] { return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, F.r, F.e, L0.g, 0, s); });
     if ((rc = run_pass(P, 0, OP_RESIDUAL, F.e, F.tm_e, F.r, L0.t, s))) return rc;
-    return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, L0.t, F.e, L0.g, 1, s);
+    return K(P, "coarsest", s, [&] { return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, L0.t, F.e, L0.g, 1, s); });
   }
   // down: fine residual, then restriction to the coarsest level
   const void* r0 = F.r;
@@ -296,18 +337,28 @@ int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
     if ((rc = run_pass(P, 0, OP_RESIDUAL, F.e, F.tm_e, F.r, L0.t, s))) return rc;
     r0 = L0.t;
   }
-  if ((rc = launch_restrict(T, r0, L0.g, P->lv[1].r, P->lv[1].g, s))) return rc;
+  if ((rc = K(P, "restrict:L0", s, [&] { return launch_restrict(T, r0, L0.g, P->lv[1].r, P->lv[1].g, s); })))
+    return rc;
   for (int l = 1; l + 1 < nl; ++l)
-    if ((rc = launch_restrict(T, P->lv[l].r, P->lv[l].g, P->lv[l + 1].r, P->lv[l + 1].g, s))) return rc;
+    if ((rc = K(P, "restrict:" + lvl(l), s,
+                [&] { return launch_restrict(T, P->lv[l].r, P->lv[l].g, P->lv[l + 1].r, P->lv[l + 1].g, s); })))
+      return rc;
   Level& C = P->lv[nl - 1];
-  if ((rc = launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, C.r, C.e, C.g, 0, s))) return rc;
+  if ((rc = K(P, "coarsest", s,
+              [&] { return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, C.r, C.e, C.g, 0, s); })))
+    return rc;
   // up: prolongation then one Jacobi sweep per level
   for (int l = nl - 2; l >= 1; --l) {
     Level& L = P->lv[l];
-    if ((rc = launch_prolong_base(T, P->lv[l + 1].e, P->lv[l + 1].g, L.t, nullptr, L.g, s))) return rc;
+    if ((rc = K(P, "prolong:" + lvl(l), s,
+                [&] { return launch_prolong_base(T, P->lv[l + 1].e, P->lv[l + 1].g, L.t, nullptr, L.g, s); })))
+      return rc;
     if ((rc = run_pass(P, l, OP_JACOBI, L.t, &L.tm_t, L.r, L.e, s))) return rc;
   }
-  if ((rc = launch_prolong_base(T, P->lv[1].e, P->lv[1].g, L0.t, first ? nullptr : F.e, L0.g, s))) return rc;
+  if ((rc = K(P, "prolong:L0", s, [&] {
+         return launch_prolong_base(T, P->lv[1].e, P->lv[1].g, L0.t, first ? nullptr : F.e, L0.g, s);
+       })))
+    return rc;
   return run_pass(P, 0, OP_JACOBI, L0.t, &L0.tm_t, F.r, F.e, s);
 }
 
@@ -332,17 +383,23 @@ int outer_residual(PlanImpl* P, cudaStream_t s, double* norm2) {
   a.zchunk = P->cfg64.zchunk;
   int rc;
   if ((rc = check_cuda(cudaMemsetAsync(norm2, 0, sizeof(double), s), "zero norm"))) return rc;
-  return launch_pass(NN4_F64, OP_RESIDUAL, a, P->x64, P->vc ? P->k64 : nullptr, P->cfg64, s, &P->tm_x64,
-                     P->vc ? &P->tm_k64 : nullptr);
+  return K(P, "pass64:residual", s, [&] {
+    return launch_pass(NN4_F64, OP_RESIDUAL, a, P->x64, P->vc ? P->k64 : nullptr, P->cfg64, s, &P->tm_x64,
+                       P->vc ? &P->tm_k64 : nullptr);
+  });
 }
 
 // One defect-correction iteration: rT = r; e = cycles(rT); x += e; r = b - A x (norm -> scal[0]).
 int iteration_cycles(PlanImpl* P, cudaStream_t s) {
   Level& L0 = P->lv[0];
   int rc;
-  if (P->T != NN4_F64 && (rc = launch_to_inner(P->T, P->r64, P->g64, L0.r, L0.g, s))) return rc;
+  if (P->T != NN4_F64 &&
+      (rc = K(P, "pointwise:to_inner", s, [&] { return launch_to_inner(P->T, P->r64, P->g64, L0.r, L0.g, s); })))
+    return rc;
   if ((rc = inner_solve(P, s))) return rc;
-  if ((rc = launch_add_correction(P->T, P->x64, P->g64, L0.e, L0.g, s))) return rc;
+  if ((rc = K(P, "pointwise:add_correction", s,
+              [&] { return launch_add_correction(P->T, P->x64, P->g64, L0.e, L0.g, s); })))
+    return rc;
   return outer_residual(P, s, P->scal + 0);
 }
 
@@ -353,9 +410,13 @@ int iteration_fcg(PlanImpl* P, int par, cudaStream_t s) {
   int rc;
   if ((rc = inner_solve(P, s))) return rc;  // z = L0.e from rT = L0.r
   if ((rc = check_cuda(cudaMemsetAsync(P->scal + 2, 0, sizeof(double), s), "zero zq"))) return rc;
-  if ((rc = launch_dot_zq(P->T, L0.e, L0.g, P->q64[old], P->g64, P->scal + 2, s))) return rc;
-  if ((rc = launch_new_direction(P->T, L0.e, L0.g, P->p64[old], P->p64[par], P->g64, P->scal + 2,
-                                 P->scal + 3 + old, s)))
+  if ((rc = K(P, "pointwise:dot", s,
+              [&] { return launch_dot_zq(P->T, L0.e, L0.g, P->q64[old], P->g64, P->scal + 2, s); })))
+    return rc;
+  if ((rc = K(P, "pointwise:direction", s, [&] {
+         return launch_new_direction(P->T, L0.e, L0.g, P->p64[old], P->p64[par], P->g64, P->scal + 2,
+                                     P->scal + 3 + old, s);
+       })))
     return rc;
   if ((rc = check_cuda(cudaMemsetAsync(P->scal + 3 + par, 0, sizeof(double), s), "zero pq"))) return rc;
   if ((rc = check_cuda(cudaMemsetAsync(P->scal + 5 + par, 0, sizeof(double), s), "zero pr"))) return rc;
@@ -367,13 +428,17 @@ int iteration_fcg(PlanImpl* P, int par, cudaStream_t s) {
   a.norm2 = P->scal + 3 + par;
   a.dot2 = P->scal + 5 + par;
   a.zchunk = P->cfg64.zchunk;
-  if ((rc = launch_pass(NN4_F64, OP_MATVEC, a, P->p64[par], P->vc ? P->k64 : nullptr, P->cfg64, s,
-                        &P->tm_p64[par], P->vc ? &P->tm_k64 : nullptr)))
+  if ((rc = K(P, "pass64:matvec", s, [&] {
+         return launch_pass(NN4_F64, OP_MATVEC, a, P->p64[par], P->vc ? P->k64 : nullptr, P->cfg64, s,
+                            &P->tm_p64[par], P->vc ? &P->tm_k64 : nullptr);
+       })))
     return rc;
   if ((rc = check_cuda(cudaMemsetAsync(P->scal + 0, 0, sizeof(double), s), "zero norm"))) return rc;
-  return launch_fcg_update(P->T, P->x64, P->r64, P->p64[par], P->q64[par], P->g64,
-                           P->T == NN4_F64 ? nullptr : L0.r, L0.g, P->scal + 5 + par, P->scal + 3 + par,
-                           P->scal + 0, s);
+  return K(P, "pointwise:fcg_update", s, [&] {
+    return launch_fcg_update(P->T, P->x64, P->r64, P->p64[par], P->q64[par], P->g64,
+                             P->T == NN4_F64 ? nullptr : L0.r, L0.g, P->scal + 5 + par, P->scal + 3 + par,
+                             P->scal + 0, s);
+  });
 }
 
 int iteration(PlanImpl* P, int it, cudaStream_t s) {
@@ -381,7 +446,7 @@ int iteration(PlanImpl* P, int it, cudaStream_t s) {
 }
 
 int ensure_graphs(PlanImpl* P) {
-  if (!P->o.use_graph || P->graph[0]) return NN4_OK;
+  if (!P->o.use_graph || P->o.profile || P->graph[0]) return NN4_OK;
   int rc;
   if (!P->graph_stream &&
       (rc = check_cuda(cudaStreamCreateWithFlags(&P->graph_stream, cudaStreamNonBlocking), "graph stream")))
@@ -391,7 +456,10 @@ int ensure_graphs(PlanImpl* P) {
     cudaGraph_t g;
     if ((rc = check_cuda(cudaStreamBeginCapture(P->graph_stream, cudaStreamCaptureModeThreadLocal), "begin capture")))
       return rc;
+    const int64_t k0 = P->kernels;
     rc = iteration(P, par, P->graph_stream);
+    P->graph_kernels[par] = P->kernels - k0;
+    P->kernels = k0;
     cudaError_t e = cudaStreamEndCapture(P->graph_stream, &g);
     if (rc) return rc;
     if ((rc = check_cuda(e, "end capture"))) return rc;
@@ -403,8 +471,9 @@ int ensure_graphs(PlanImpl* P) {
 }
 
 int launch_iteration(PlanImpl* P, int it, cudaStream_t s) {
-  if (P->o.use_graph) {
+  if (P->o.use_graph && !P->o.profile) {
     const int par = P->o.outer == NN4_OUTER_FCG ? (it & 1) : 0;
+    P->kernels += P->graph_kernels[par];
     return check_cuda(cudaGraphLaunch(P->graph[par], s), "graph launch");
   }
   return iteration(P, it, s);
@@ -426,6 +495,10 @@ void destroy(PlanImpl* P) {
   for (auto& g : P->graph)
     if (g) cudaGraphExecDestroy(g);
   if (P->graph_stream) cudaStreamDestroy(P->graph_stream);
+  for (auto& r : P->recs) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
   for (void* p : P->allocs) cudaFree(p);
   if (P->host_hist) cudaFreeHost(P->host_hist);
   delete P;
@@ -465,11 +538,15 @@ int solve_device(PlanImpl* P, double rtol, int32_t max_iters, nn4_solve_info* in
   if ((rc = ensure_graphs(P))) return rc;
   // ||b||^2 over free nodes, initial residual
   if ((rc = check_cuda(cudaMemsetAsync(P->scal + 1, 0, sizeof(double), s), "zero"))) return rc;
-  if ((rc = launch_norm_masked(P->b64, P->g64, P->scal + 1, s))) return rc;
+  const int64_t kstart = P->kernels;
+  if ((rc = K(P, "pointwise:norm", s, [&] { return launch_norm_masked(P->b64, P->g64, P->scal + 1, s); }))) return rc;
   if ((rc = outer_residual(P, s, P->scal + 0))) return rc;
   if (P->o.outer == NN4_OUTER_FCG) {
     // r64 holds the residual; rT for the first inner solve; p_old = q_old = 0, p.q_old = 1
-    if (P->T != NN4_F64 && (rc = launch_to_inner(P->T, P->r64, P->g64, P->lv[0].r, P->lv[0].g, s))) return rc;
+    if (P->T != NN4_F64 && (rc = K(P, "pointwise:to_inner", s, [&] {
+                              return launch_to_inner(P->T, P->r64, P->g64, P->lv[0].r, P->lv[0].g, s);
+                            })))
+      return rc;
     if (P->T == NN4_F64 &&
         (rc = check_cuda(cudaMemcpyAsync(P->lv[0].r, P->r64, field_bytes(P->g64, NN4_F64), cudaMemcpyDeviceToDevice, s),
                          "copy r")))
@@ -530,6 +607,7 @@ int solve_device(PlanImpl* P, double rtol, int32_t max_iters, nn4_solve_info* in
     info->iterations = it;
     info->cycles = it * P->o.inner_cycles;
     info->rel_res = final_rel;
+    info->kernels = P->kernels - kstart;
     if (info->history)
       for (int t = 0; t <= it && t < info->history_len; ++t) info->history[t] = std::sqrt(h[t]) / bn;
   }
@@ -558,6 +636,7 @@ void nn4_plan_opts_default(nn4_plan_opts* o) {
   o->omega = 2.0 / 3.0;
   o->use_graph = 1;
   o->check_every = 1;
+  o->profile = 0;
 }
 
 int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opts, nn4_plan* out) {
@@ -741,6 +820,54 @@ int nn4_pressure_solve_host(nn4_plan p, const double* b_host, double* x_host, do
       (rc = check_cuda(cudaStreamSynchronize(s), "sync")))
     return rc;
   return st;
+}
+
+int nn4_plan_profile(nn4_plan p, nn4_kernel_time* out, int32_t cap) {
+  if (!p) return set_error(NN4_EINVAL, "NULL plan");
+  PlanImpl* P = p->impl;
+  int rc;
+  if ((rc = check_cuda(cudaDeviceSynchronize(), "sync"))) return rc;
+  std::vector<std::string> names;
+  std::vector<int64_t> cnt;
+  std::vector<double> tot;
+  for (auto& r : P->recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.e0, r.e1);
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+    size_t i = 0;
+    while (i < names.size() && names[i] != r.name) ++i;
+    if (i == names.size()) {
+      names.push_back(r.name);
+      cnt.push_back(0);
+      tot.push_back(0.0);
+    }
+    cnt[i] += 1;
+    tot[i] += ms;
+  }
+  P->recs.clear();
+  for (size_t i = 0; i < names.size() && (int)i < cap; ++i) {
+    std::strncpy(out[i].name, names[i].c_str(), sizeof(out[i].name) - 1);
+    out[i].name[sizeof(out[i].name) - 1] = 0;
+    out[i].launches = cnt[i];
+    out[i].total_ms = tot[i];
+  }
+  return (int)names.size();
+}
+
+int nn4_plan_query(nn4_plan p, nn4_plan_info* out) {
+  if (!p || !out) return set_error(NN4_EINVAL, "NULL argument");
+  PlanImpl* P = p->impl;
+  std::memset(out, 0, sizeof(*out));
+  out->levels = (int)P->lv.size();
+  for (size_t l = 0; l < P->lv.size() && l < 16; ++l) {
+    out->n[l][0] = P->lv[l].g.nx;
+    out->n[l][1] = P->lv[l].g.ny;
+    out->n[l][2] = P->lv[l].g.nz;
+  }
+  out->coarsest_free = P->nfree;
+  out->device_bytes = (int64_t)P->device_bytes;
+  return NN4_OK;
 }
 
 }  // extern "C"

@@ -41,12 +41,22 @@ class _Grid(ctypes.Structure):
 class _PlanOpts(ctypes.Structure):
     _fields_ = [("inner", ctypes.c_int), ("inner_cycles", ctypes.c_int32), ("outer", ctypes.c_int32),
                 ("omega", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("check_every", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32)]
 
 
 class _SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("cycles", ctypes.c_int32), ("rel_res", ctypes.c_double),
-                ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int32)]
+                ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int32),
+                ("kernels", ctypes.c_int64)]
+
+
+class _KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("n", (ctypes.c_int32 * 3) * 16), ("coarsest_free", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -75,6 +85,8 @@ def lib():
             "nn4_vcycle": (ctypes.c_int, [vp, vp, vp, vp]),
             "nn4_pressure_solve": (ctypes.c_int, [vp, vp, vp, dbl, i32, ctypes.POINTER(_SolveInfo), vp]),
             "nn4_pressure_solve_host": (ctypes.c_int, [vp, vp, vp, dbl, i32, ctypes.POINTER(_SolveInfo), vp]),
+            "nn4_plan_profile": (ctypes.c_int, [vp, ctypes.POINTER(_KernelTime), i32]),
+            "nn4_plan_query": (ctypes.c_int, [vp, ctypes.POINTER(_PlanInfo)]),
             "nn4_last_error": (ctypes.c_char_p, []),
             "nn4_device_error": (ctypes.c_int, []),
             "nn4_version": (ctypes.c_char_p, []),
@@ -204,11 +216,12 @@ class Plan:
     """Multigrid hierarchy for one grid (and optional FP64 coefficient field k)."""
 
     def __init__(self, grid, k=None, inner=F64, inner_cycles=1, outer=OUTER_CYCLES, omega=2.0 / 3.0,
-                 use_graph=True, check_every=1):
+                 use_graph=True, check_every=1, profile=False):
         o = _PlanOpts()
         lib().nn4_plan_opts_default(ctypes.byref(o))
         o.inner, o.inner_cycles, o.outer = int(inner), int(inner_cycles), int(outer)
         o.omega, o.use_graph, o.check_every = float(omega), int(bool(use_graph)), int(check_every)
+        o.profile = int(bool(profile))
         self.grid = grid
         self.inner = inner
         self._k = k  # keep the coefficient alive while the plan exists
@@ -242,7 +255,21 @@ class Plan:
             _check(code)
         n = min(history_len, info.iterations + 1)
         return {"status": code, "iterations": info.iterations, "cycles": info.cycles,
-                "rel_res": info.rel_res, "history": list(hist[:n])}
+                "rel_res": info.rel_res, "history": list(hist[:n]), "kernels": info.kernels}
+
+    def profile(self):
+        """{kernel category: (launches, total ms)} since the last call (profile plans only)."""
+        buf = (_KernelTime * 256)()
+        n = lib().nn4_plan_profile(self._h, buf, 256)
+        if n < 0:
+            _check(n)
+        return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(min(n, 256))}
+
+    def query(self):
+        q = _PlanInfo()
+        _check(lib().nn4_plan_query(self._h, ctypes.byref(q)))
+        return {"levels": q.levels, "n": [tuple(q.n[l]) for l in range(q.levels)],
+                "coarsest_free": q.coarsest_free, "device_bytes": q.device_bytes}
 
     def solve(self, b, x, rtol=1e-8, max_iters=200, history_len=512, stream=None):
         """Pressure solve on device FP64 storage tensors b, x (x: initial guess, then solution)."""

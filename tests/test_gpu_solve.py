@@ -1,0 +1,185 @@
+"""GPU parity of the V-cycle and the pressure solves against the FP64 oracle.
+
+* plain FP64: every V-cycle agrees with the oracle's cycle to 1e-12 relative (the oracle runs
+  the same sawtooth cycle), and the solve's residual history agrees to 1e-12;
+* mixed precision (FP32 / BF16 storage, FP64 outer loop): the solution agrees with the oracle's
+  converged FP64 solution of A x = b to 1e-8 relative (after removing the mean for the singular
+  all-natural problem);
+* flexible CG with Galerkin coarse operators for a 1000:1 density sphere: FP64 per-iteration
+  parity with the oracle's flexible CG, mixed-precision solution error <= 1e-8.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import direct, fem, mg
+from synth import sphere_ramp_field, standard_normal, uniform01
+from tests.gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _nn4():
+    from paper_2401_06755_gb300 import nn4
+    return nn4
+
+
+def _grids(n, h, bc):
+    nn4 = _nn4()
+    g = mg.Grid(tuple(n), tuple(h), tuple(bc))
+    G = nn4.Grid(tuple(n), tuple(h), tuple(nn4.DIRICHLET if d else nn4.NATURAL for d in bc))
+    return g, G
+
+
+def _rhs(g, seed):
+    b = fem.lumped_mass(g.shape, g.h) * standard_normal(seed, int(np.prod(g.shape))).reshape(g.shape)
+    b[mg.dirichlet_mask(g)] = 0.0
+    if mg.is_singular(g):
+        b -= b.mean()
+    return b
+
+
+def _sphere_k(g, seed=0, ratio=1000.0):
+    c = 0.3 + 0.4 * uniform01(seed, 3)
+    C = sphere_ramp_field(g.n, g.h, c, 0.2, 2 * max(g.h))
+    return 1.0 / (ratio * C + (1.0 - C))
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+CYCLE_CASES = [
+    ((33, 33, 33), (1 / 32,) * 3, (True,) * 6, False),
+    ((17, 9, 33), (1 / 16, 1 / 8, 1 / 32), (False,) * 5 + (True,), False),
+    ((33, 17, 17), (1 / 32, 1 / 16, 1 / 16), (False,) * 6, False),
+    ((17, 17, 17), (1 / 16,) * 3, (False,) * 6, True),
+    ((17, 9, 17), (1 / 16, 1 / 8, 1 / 16), (False,) * 5 + (True,), True),
+    ((3, 3, 3), (0.5,) * 3, (True,) * 6, False),
+]
+
+
+@pytest.mark.parametrize("ci", range(len(CYCLE_CASES)))
+def test_vcycle_fp64_per_cycle(ci):
+    """nn4_vcycle on FP64 arrays reproduces the oracle's sawtooth cycle to 1e-12 per cycle."""
+    need_gpu()
+    nn4 = _nn4()
+    n, h, bc, vc = CYCLE_CASES[ci]
+    g, G = _grids(n, h, bc)
+    k = _sphere_k(g) if vc else None
+    b = _rhs(g, 1 + ci)
+    lv = mg.Levels(g, k)
+    plan = nn4.Plan(G, nn4.to_field(k, G) if vc else None)
+    B, X = nn4.to_field(b, G), nn4.field(G)
+    x = np.zeros(g.shape)
+    for c in range(6):
+        x = mg.vcycle(lv, x, b)
+        plan.vcycle(B, X)
+        xg = nn4.nodes(X, G).cpu().numpy()
+        assert _rel(xg, x) <= 1e-12, f"cycle {c}: {_rel(xg, x):.3e}"
+
+
+def test_solve_fp64_fixed_cycles_history():
+    """Config-1 style: 33^3 Dirichlet, 20 cycles; history and solution match the oracle."""
+    need_gpu()
+    nn4 = _nn4()
+    g, G = _grids((33,) * 3, (1 / 32,) * 3, (True,) * 6)
+    b = fem.lumped_mass(g.shape, g.h) * standard_normal(0, 33 ** 3).reshape(g.shape)
+    b[mg.dirichlet_mask(g)] = 0.0
+    xo, ho = mg.pressure_solve(g, b, fixed_cycles=20)
+    for graph in (True, False):
+        plan = nn4.Plan(G, use_graph=graph)
+        B, X = nn4.to_field(b, G), nn4.field(G)
+        info = plan.solve(B, X, rtol=0.0, max_iters=20)
+        assert info["iterations"] == 20
+        hg = np.array(info["history"])
+        assert np.all(np.abs(hg - np.array(ho)) <= 1e-12 * np.maximum(hg, 1e-3))
+        assert _rel(nn4.nodes(X, G).cpu().numpy(), xo) <= 1e-12
+
+
+@pytest.mark.parametrize("inner", ["f32", "bf16"])
+@pytest.mark.parametrize("outer", ["cycles", "fcg"])
+def test_solve_mixed_constant_coefficient(inner, outer):
+    need_gpu()
+    nn4 = _nn4()
+    g, G = _grids((65, 33, 33), (1 / 64, 1 / 32, 1 / 32), (False,) * 5 + (True,))
+    b = _rhs(g, 4)
+    xref = direct.solve_cg(g, b, rtol=1e-14)
+    plan = nn4.Plan(G, inner=nn4.F32 if inner == "f32" else nn4.BF16, inner_cycles=2,
+                    outer=nn4.OUTER_CYCLES if outer == "cycles" else nn4.OUTER_FCG)
+    B, X = nn4.to_field(b, G), nn4.field(G)
+    info = plan.solve(B, X, rtol=1e-11, max_iters=200)
+    assert info["status"] == nn4.OK and info["rel_res"] <= 1e-11
+    assert _rel(nn4.nodes(X, G).cpu().numpy(), xref) <= 1e-8
+
+
+def test_fcg_fp64_matches_oracle_sphere():
+    """Flexible CG + Galerkin cycle at 33^3, 1000:1 sphere, all-natural: FP64 per-iteration
+    residual history matches the oracle's; the solution matches the dense-free CG reference."""
+    need_gpu()
+    nn4 = _nn4()
+    g, G = _grids((33,) * 3, (1 / 32,) * 3, (False,) * 6)
+    k = _sphere_k(g)
+    b = _rhs(g, 1)
+    xo, ho = mg.pressure_solve_fcg(g, b, k=k, rtol=1e-10, max_iters=80)
+    plan = nn4.Plan(G, nn4.to_field(k, G), outer=nn4.OUTER_FCG)
+    B, X = nn4.to_field(b, G), nn4.field(G)
+    info = plan.solve(B, X, rtol=1e-10, max_iters=80)
+    hg = np.array(info["history"])
+    m = min(len(hg), len(ho))
+    # the recurrences agree to rounding while the residual is far above rounding level
+    assert np.all(np.abs(hg[:m] - np.array(ho[:m])) <= 1e-9 * np.maximum(np.array(ho[:m]), 1e-6))
+    xg = nn4.nodes(X, G).cpu().numpy()
+    assert _rel(xg - xg.mean(), xo - xo.mean()) <= 1e-9
+
+
+@pytest.mark.parametrize("inner", ["f32", "bf16"])
+def test_fcg_mixed_sphere_error(inner):
+    """Precision form at 65^3: mixed flexible CG reaches the FP64 solution to <= 1e-8."""
+    need_gpu()
+    nn4 = _nn4()
+    g, G = _grids((65,) * 3, (1 / 64,) * 3, (False,) * 6)
+    k = _sphere_k(g)
+    b = _rhs(g, 1)
+    xref, _ = mg.pressure_solve_fcg(g, b, k=k, rtol=1e-13, max_iters=200)
+    plan = nn4.Plan(G, nn4.to_field(k, G), inner=nn4.F32 if inner == "f32" else nn4.BF16,
+                    inner_cycles=2, outer=nn4.OUTER_FCG)
+    B, X = nn4.to_field(b, G), nn4.field(G)
+    info = plan.solve(B, X, rtol=1e-10, max_iters=200)
+    assert info["status"] == nn4.OK
+    xg = nn4.nodes(X, G).cpu().numpy()
+    m = fem.lumped_mass(g.shape, g.h)
+    mean = lambda v: (m * v).sum() / m.sum()
+    assert _rel(xg - mean(xg), xref - mean(xref)) <= 1e-8
+
+
+def test_host_buffers_equal_device_solve():
+    need_gpu()
+    nn4 = _nn4()
+    g, G = _grids((33, 17, 17), (1 / 32, 1 / 16, 1 / 16), (False,) * 5 + (True,))
+    b = _rhs(g, 9)
+    plan = nn4.Plan(G, inner=nn4.F32, inner_cycles=2)
+    B, X = nn4.to_field(b, G), nn4.field(G)
+    i1 = plan.solve(B, X, rtol=1e-10)
+    bh = torch.tensor(b).contiguous().pin_memory()
+    xh = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
+    i2 = plan.solve_host(bh, xh, rtol=1e-10)
+    assert i1["iterations"] == i2["iterations"]
+    np.testing.assert_array_equal(nn4.nodes(X, G).cpu().numpy(), xh.numpy())
+
+
+def test_error_paths():
+    need_gpu()
+    nn4 = _nn4()
+    g, G = _grids((17,) * 3, (1 / 16,) * 3, (True,) * 6)
+    plan = nn4.Plan(G)
+    b = _rhs(g, 2)
+    b[5, 5, 5] = np.nan
+    with pytest.raises(nn4.NN4Error) as e:
+        plan.solve(nn4.to_field(b, G), nn4.field(G), rtol=1e-8)
+    assert e.value.code == nn4.ENONFINITE
+    b = _rhs(g, 2)
+    info = plan.solve(nn4.to_field(b, G), nn4.field(G), rtol=1e-14, max_iters=3)
+    assert info["status"] == nn4.ENOCONV and info["iterations"] == 3
+    assert nn4.device_error() == nn4.OK
