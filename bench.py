@@ -1,0 +1,370 @@
+"""Benchmark of the pressure solve at 257^3 nodes (256^3 elements) to 1e-8 relative residual.
+
+Workload (the precision form): div((1/rho) grad p) = f on the unit cube with zero-derivative
+walls, rho = 1 inside a seeded sphere of radius 0.2 and 1000 outside, smoothed over 2 cells;
+f ~ N(0,1), made zero-mean with the lumped-mass weights.  One step = one complete pressure
+solve from x = 0 to ||b - A x|| / ||b|| <= 1e-8 with inputs resident in HBM: FP64 flexible-CG
+outer loop, V-cycle preconditioner stored in BF16 (or FP32) with FP32 arithmetic.  The plain
+FP64 GPU path (same outer loop, FP64 cycles) is timed beside it.
+
+Contract: `python bench.py --gpus N --steps K --warmup W [--impl reference]` prints one JSON line
+(rank 0).  For N > 1 (torchrun) every rank solves its own copy (replicas; weak scaling).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "pressure solves/s at 257^3 to 1e-8 rel (mixed precision)"
+UNIT = "solves/s"
+N_NODES = 257
+RTOL = 1e-8
+
+
+def workload(n=N_NODES, seed_sphere=0, seed_f=1, ratio=1000.0):
+    """Host inputs of the precision-form workload: coefficient k = 1/rho and right-hand side b."""
+    from synth import sphere_ramp_field, standard_normal, uniform01
+    h = 1.0 / (n - 1)
+    shape = (n, n, n)
+    centre = 0.3 + 0.4 * uniform01(seed_sphere, 3)
+    C = sphere_ramp_field((n, n, n), (h, h, h), centre, 0.2, 2 * h)
+    rho = ratio * C + (1.0 - C)
+    k = 1.0 / rho
+    # lumped nodal volume: h^3 times 1/2 per boundary the node lies on (tensor product)
+    w1 = np.full(n, h)
+    w1[0] = w1[-1] = h / 2
+    m = w1[:, None, None] * w1[None, :, None] * w1[None, None, :]
+    f = standard_normal(seed_f, n ** 3).reshape(shape)
+    f -= (m * f).sum() / m.sum()
+    b = -m * f          # weak form of div((1/rho) grad p) = f with A = -div(k grad)
+    b -= b.mean()       # exact solvability of the singular all-natural system
+    return h, k, b
+
+
+# ---------------------------------------------------------------- clocks sampling
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+def oracle_sample(n=65):
+    """Times the FP64 oracle's full solve of the same recipe at n^3 on the host (1 thread)."""
+    code = (
+        "import os,sys,time,json; sys.path.insert(0,%r)\n"
+        "import numpy as np\n"
+        "from bench import workload\n"
+        "from oracle import mg\n"
+        "h,k,b=workload(%d)\n"
+        "g=mg.Grid((%d,)*3,(h,)*3)\n"
+        "t=time.perf_counter(); x,hist=mg.pressure_solve_fcg(g,b,k=k,rtol=%g,max_iters=300); dt=time.perf_counter()-t\n"
+        "print(json.dumps({'seconds':dt,'iters':len(hist)-1,'rel':hist[-1]}))\n" % (ROOT, n, n, RTOL))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    scale = (N_NODES ** 3) / float(n ** 3)
+    r["solves_per_s"] = 1.0 / (r["seconds"] * scale)
+    r["sample"] = (f"oracle (numpy/scipy FP64) flexible-CG solve of the same recipe at {n}^3 nodes "
+                   f"({r['iters']} iterations, {r['seconds']:.1f} s), scaled by the node ratio "
+                   f"{scale:.1f} to 257^3")
+    return r
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg = config_dict(args)
+    times = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(args.ref_n)
+        if i >= args.warmup:
+            times.append(r["solves_per_s"])
+        last = r
+    value = statistics.median(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def config_dict(args):
+    return {"workload": "precision form: 257^3 nodes (256^3 elements), div((1/rho) grad p) = f, "
+                        "1000:1 seeded sphere R=0.2 smoothed over 2 cells, zero-derivative walls, "
+                        "f ~ N(0,1) zero-mean, x0 = 0, to 1e-8 relative residual",
+            "inner": args.inner, "outer": "fcg (FP64)", "inner_cycles": args.m,
+            "coarse_operators": "Galerkin", "smoother": "weighted Jacobi omega=2/3, 1 sweep per level",
+            "l2": "inputs larger than L2 (b, x, k: 3 x 144 MB FP64 plus the hierarchy)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--m", type=int, default=2, help="V-cycles per outer iteration")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--ref-n", type=int, default=65)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="time the mixed solve only (for profiler runs; no JSON contract)")
+    ap.add_argument("--n", type=int, default=N_NODES, help="nodes per axis (profiler runs on smaller cases)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2401_06755_gb300 import nn4
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = args.n
+    h, k_host, b_host = workload(n)
+    G = nn4.Grid((n, n, n), (h, h, h))
+    K = nn4.to_field(k_host, G)
+    B = nn4.to_field(b_host, G)
+    X = nn4.field(G)
+    inner = nn4.BF16 if args.inner == "bf16" else nn4.F32
+    plan = nn4.Plan(G, K, inner=inner, inner_cycles=args.m, outer=nn4.OUTER_FCG, check_every=2)
+    stream = torch.cuda.current_stream()
+
+    def solve(p, x):
+        x.zero_()
+        return p.solve(B, x, rtol=RTOL, max_iters=400, stream=stream)
+
+    for _ in range(args.warmup):
+        info = solve(plan, X)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        ev0.record(stream)
+        kernels = 0
+        iters = []
+        for _ in range(args.steps):
+            info = solve(plan, X)
+            kernels += info["kernels"]
+            iters.append(info["iterations"])
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per = ms / args.steps
+    value = world * args.steps / (ms / 1000.0)
+    if args.only_mixed:
+        if rank == 0:
+            print(json.dumps({"n": n, "ms_per_solve": ms_per, "iterations": iters, "kernels": kernels}))
+        return
+    rel_res = info["rel_res"]
+    x_mixed = nn4.nodes(X, G).clone()
+
+    # plain FP64 GPU path on the same system
+    plan64 = nn4.Plan(G, K, inner=nn4.F64, inner_cycles=1, outer=nn4.OUTER_FCG, check_every=2)
+    X64 = nn4.field(G)
+    solve(plan64, X64)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.fp64_steps):
+        i64 = solve(plan64, X64)
+    e1.record(stream)
+    barrier()
+    ms64 = e0.elapsed_time(e1) / args.fp64_steps
+    x64 = nn4.nodes(X64, G)
+    # error of the mixed solution against the FP64 GPU solution (means removed: singular system)
+    d = (x_mixed - x_mixed.mean()) - (x64 - x64.mean())
+    err_vs_fp64 = float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(x64 - x64.mean()))
+
+    # one V-cycle of each hierarchy, timed on its own
+    def vcycle_ms(p, dtype, reps=10):
+        bt = nn4.to_field(b_host, G, dtype)
+        xt = nn4.field(G, dtype)
+        p.vcycle(bt, xt)
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            p.vcycle(bt, xt)
+        z.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / reps
+    vc_inner = vcycle_ms(plan, torch.bfloat16 if inner == nn4.BF16 else torch.float32)
+    vc_64 = vcycle_ms(plan64, torch.float64, reps=3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the call
+    bh = torch.from_numpy(np.ascontiguousarray(b_host)).pin_memory()
+    xh = torch.zeros((n, n, n), dtype=torch.float64).pin_memory()
+    plan.solve_host(bh, xh, rtol=RTOL, max_iters=400)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, args.steps // 2)
+    for _ in range(e2e_steps):
+        xh.zero_()
+        plan.solve_host(bh, xh, rtol=RTOL, max_iters=400)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    nbytes = n ** 3 * 8
+
+    # per-kernel durations from an eagerly launched, event-timed solve of the same plan setup
+    prof_plan = nn4.Plan(G, K, inner=inner, inner_cycles=args.m, outer=nn4.OUTER_FCG, check_every=2,
+                         profile=True)
+    solve(prof_plan, X)
+    prof_plan.profile()
+    solve(prof_plan, X)
+    prof = prof_plan.profile()
+    total_prof = sum(v[1] for v in prof.values())
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    roof = roofline_entry(top, n, MEASURED.get("fp64_tflops", 1.20), MEASURED.get("hbm_gbs", 6674.5))
+    inner_kernels = {kk: vv for kk, vv in prof.items() if kk.startswith("pass:") and kk.endswith(":L0")}
+    inner_top = max(inner_kernels.items(), key=lambda kv: kv[1][1]) if inner_kernels else None
+    roof_inner = roofline_entry(inner_top, n, 0, MEASURED.get("hbm_gbs", 6674.5),
+                                dtype=args.inner) if inner_top else None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            r = oracle_sample(args.ref_n)
+            cpu = {"value": r["solves_per_s"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": r["sample"]}
+        except Exception as ex:  # reported, not fatal
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": f"{args.inner}-storage/f32-compute inner, f64 outer",
+            "data": "synthetic", "config": config_dict(args),
+            "iterations_per_solve": statistics.median(iters), "rel_res": rel_res,
+            "error_vs_fp64_gpu": err_vs_fp64,
+            "fp64_path": {"solves_per_s": 1000.0 / ms64, "ms_per_solve": ms64, "iterations": i64["iterations"]},
+            "speedup_vs_fp64": (1000.0 / ms_per) / (1000.0 / ms64),
+            "vcycle_ms": {args.inner: vc_inner, "f64": vc_64},
+            "roofline": roof, "roofline_inner": roof_inner,
+            "kernel_shares": {kk: round(vv[1] / total_prof, 4) for kk, vv in
+                              sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": kernels, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- roofline
+def _load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+    except OSError:
+        d = {}
+    return {"hbm_gbs": d.get("hbm_gbs", 6674.5), "fp64_tflops": 1.20}
+
+
+MEASURED = _load_peaks()
+
+# Algorithmic work per fine node ("Roofline accounting"):
+#  FP64 matvec of Eq. k-T with the sum-factorised interior stencil: L x and L (k x) and L k at
+#  23 flops each (8 neighbour-class multiply-adds on 7 partial sums), plus 7 flops to combine
+#  -> 76 FP64 flops per node.  Inner stencil passes move (fields read + written) x storage bytes.
+FLOPS_PER_NODE = {"pass64:matvec": 76.0, "pass64:residual": 77.0}
+FIELDS_PER_NODE = {"pass:residual:L0": 4, "pass:jacobi:L0": 4, "restrict:L0": 1.125, "prolong:L0": 2.125}
+STORE = {"bf16": 2, "f32": 4}
+
+
+def roofline_entry(item, n, fp64_tflops, hbm_gbs, dtype=None):
+    name, (launches, total_ms) = item
+    avg_ms = total_ms / max(1, launches)
+    nodes = float(n) ** 3
+    if name in FLOPS_PER_NODE:
+        achieved = FLOPS_PER_NODE[name] * nodes / (avg_ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp64_tflops, "traffic": None, "avg_ms": avg_ms,
+                "peak_note": "FP64 FMA pipe, measured 1.20 TFLOP/s on this GB300 (2 FP64 FMA/clk/SM x 152 SMs)"}
+    if name in FIELDS_PER_NODE:
+        s = STORE.get(dtype, 8)
+        gbs = FIELDS_PER_NODE[name] * s * nodes / (avg_ms * 1e-3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": gbs / hbm_gbs, "traffic": None, "avg_ms": avg_ms, "peak_note": "of measured copy bandwidth"}
+    return {"kernel": name, "bound": None, "avg_ms": avg_ms}
+
+
+if __name__ == "__main__":
+    main()

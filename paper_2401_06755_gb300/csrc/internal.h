@@ -39,6 +39,10 @@ struct PassArgs {
   double* norm2;     // optional: += sum out^2 (OP_RESIDUAL) or x.out (OP_MATVEC)
   double* dot2;      // OP_MATVEC: += x.b
   int zchunk;        // output planes per block
+  // Eq. k-T with precomputed fields (optional): lk = L k (assembled, pitch g.pitch) replaces the
+  // on-the-fly stencil of k; invd = 1 / diag(A) replaces the division in Jacobi.
+  const void* lk;
+  const void* invd;
 };
 
 // Stencil pass launch configuration (chosen by the autotuner or by default).

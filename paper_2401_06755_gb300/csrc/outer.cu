@@ -84,6 +84,18 @@ __global__ void k_fcg_update(double* __restrict__ x, double* __restrict__ r, con
   block_sum_atomic(s, norm2, red);
 }
 
+// invd = 1 / (w c0 k - L k / 2): the diagonal of Eq. k-T (w = prod_d s_d / 2, c0 the interior
+// centre weight of the stencil).
+__global__ void k_inv_diag(const double* __restrict__ k, const double* __restrict__ lk, double* __restrict__ invd,
+                           LevelGeom g, double c0) {
+  NN4_FOR_NODES(g) {
+    const int j = (int)(row % g.ny), kk = (int)(row / g.ny);
+    const double w = 0.125 * ((i > 0) + (i < g.nx - 1)) * ((j > 0) + (j < g.ny - 1)) * ((kk > 0) + (kk < g.nz - 1));
+    const long long o = row * g.pitch + i;
+    invd[o] = 1.0 / (w * c0 * k[o] - 0.5 * lk[o]);
+  }
+}
+
 dim3 pw_grid(const LevelGeom& g) {
   long long rows = (long long)g.ny * g.nz;
   long long blocks = (rows + 7) / 8;
@@ -138,6 +150,12 @@ int launch_to_inner(nn4_dtype dt, const double* r, const LevelGeom& g64, void* r
                     cudaStream_t s) {
   NN4_DISPATCH(dt, to_inner_t<T>(r, g64, rT, gT, s))
 }
+int launch_inv_diag(const double* k, const double* lk, double* invd, const LevelGeom& g, double c0,
+                    cudaStream_t s) {
+  k_inv_diag<<<pw_grid(g), kPwBlock, 0, s>>>(k, lk, invd, g, c0);
+  return check_cuda(cudaGetLastError(), "inverse diagonal");
+}
+
 int launch_norm_masked(const double* v, const LevelGeom& g, double* out, cudaStream_t s) {
   k_norm_masked<<<pw_grid(g), kPwBlock, 0, s>>>(v, g, out);
   return check_cuda(cudaGetLastError(), "norm");

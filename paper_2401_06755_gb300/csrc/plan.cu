@@ -55,6 +55,7 @@ struct PlanImpl {
   PassCfg cfg64;
   double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *p64[2] = {nullptr, nullptr},
          *q64[2] = {nullptr, nullptr}, *k64 = nullptr;
+  double *lk64 = nullptr, *invd64 = nullptr;  // L k and 1/diag(A) for Eq. k-T (FP64)
   CUtensorMap tm_x64{}, tm_p64[2]{}, tm_k64{};
   // device scalars: [0] ||r||^2 (current), [1] ||b||^2, [2] z.q, [3..4] p.q by parity,
   // [5..6] p.r by parity; then the per-iteration history of ||r||^2
@@ -315,6 +316,10 @@ int run_pass(PlanImpl* P, int l, int op, const void* x, const CUtensorMap* mx, c
     return K(P, std::string("pass27:") + opname(op) + ":" + lvl(l), s,
              [&] { return launch_pass27(P->T, op, a, x, L.a27, s); });
   const bool vc0 = P->vc && l == 0;
+  if (vc0 && P->T == NN4_F64) {
+    a.lk = P->lk64;
+    a.invd = P->invd64;
+  }
   return K(P, std::string("pass:") + opname(op) + ":" + lvl(l), s, [&] {
     return launch_pass(P->T, op, a, x, vc0 ? L.k : nullptr, L.cfg, s, mx, vc0 ? &L.tm_k : nullptr);
   });
@@ -381,6 +386,7 @@ int outer_residual(PlanImpl* P, cudaStream_t s, double* norm2) {
   a.out = P->r64;
   a.norm2 = norm2;
   a.zchunk = P->cfg64.zchunk;
+  a.lk = P->lk64;
   int rc;
   if ((rc = check_cuda(cudaMemsetAsync(norm2, 0, sizeof(double), s), "zero norm"))) return rc;
   return K(P, "pass64:residual", s, [&] {
@@ -428,6 +434,7 @@ int iteration_fcg(PlanImpl* P, int par, cudaStream_t s) {
   a.norm2 = P->scal + 3 + par;
   a.dot2 = P->scal + 5 + par;
   a.zchunk = P->cfg64.zchunk;
+  a.lk = P->lk64;
   if ((rc = K(P, "pass64:matvec", s, [&] {
          return launch_pass(NN4_F64, OP_MATVEC, a, P->p64[par], P->vc ? P->k64 : nullptr, P->cfg64, s,
                             &P->tm_p64[par], P->vc ? &P->tm_k64 : nullptr);
@@ -547,10 +554,6 @@ int solve_device(PlanImpl* P, double rtol, int32_t max_iters, nn4_solve_info* in
                               return launch_to_inner(P->T, P->r64, P->g64, P->lv[0].r, P->lv[0].g, s);
                             })))
       return rc;
-    if (P->T == NN4_F64 &&
-        (rc = check_cuda(cudaMemcpyAsync(P->lv[0].r, P->r64, field_bytes(P->g64, NN4_F64), cudaMemcpyDeviceToDevice, s),
-                         "copy r")))
-      return rc;
     const size_t fb = field_bytes(P->g64, NN4_F64);
     for (int t = 0; t < 2; ++t) {
       if ((rc = check_cuda(cudaMemsetAsync(P->p64[t], 0, fb, s), "zero p"))) return rc;
@@ -666,7 +669,9 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
   {
     Level L;
     L.g = P->g64;
-    L.g.pitch = nn4_row_pitch(g->n[0], P->T);
+    // FP64 hierarchies share the caller's pitch at level 0 so that the outer residual r64 is the
+    // right-hand side of the inner cycles without a copy
+    L.g.pitch = P->T == NN4_F64 ? g->pitch : nn4_row_pitch(g->n[0], P->T);
     for (int d = 0; d < 3; ++d) L.h[d] = g->h[d];
     P->lv.push_back(L);
     while (true) {
@@ -686,7 +691,8 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
     L.L = stencil_coef(L.h);
     L.cfg = default_pass_cfg(P->T, P->vc && &L == &P->lv[0], L.g);
     const size_t fb = field_bytes(L.g, P->T);
-    if ((rc = alloc(P, &L.r, fb)) || (rc = alloc(P, &L.e, fb)) || (rc = alloc(P, &L.t, fb))) {
+    const bool alias_r = P->T == NN4_F64 && &L == &P->lv[0];
+    if ((!alias_r && (rc = alloc(P, &L.r, fb))) || (rc = alloc(P, &L.e, fb)) || (rc = alloc(P, &L.t, fb))) {
       destroy(P);
       return rc;
     }
@@ -697,6 +703,7 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
     destroy(P);
     return rc;
   }
+  if (P->T == NN4_F64) P->lv[0].r = P->r64;
   if (o.outer == NN4_OUTER_FCG) {
     for (int t = 0; t < 2; ++t)
       if ((rc = alloc(P, (void**)&P->p64[t], fb64)) || (rc = alloc(P, (void**)&P->q64[t], fb64))) {
@@ -707,8 +714,26 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
   if (P->vc) {
     if ((rc = alloc(P, (void**)&P->k64, fb64)) ||
         (rc = check_cuda(cudaMemcpy(P->k64, k, fb64, cudaMemcpyDeviceToDevice), "copy k")) ||
-        (rc = alloc(P, &P->lv[0].k, field_bytes(P->lv[0].g, P->T))) ||
-        (rc = launch_to_inner(P->T, P->k64, P->g64, P->lv[0].k, P->lv[0].g, 0))) {
+        (rc = alloc(P, (void**)&P->lk64, fb64)) || (rc = alloc(P, (void**)&P->invd64, fb64))) {
+      destroy(P);
+      return rc;
+    }
+    // L k (assembled, natural faces) and the inverse diagonal, once per plan
+    PassArgs a{};
+    a.g = P->g64;
+    a.L = P->L64;
+    a.out = P->lk64;
+    PassCfg cfg0 = default_pass_cfg(NN4_F64, false, P->g64);
+    a.zchunk = cfg0.zchunk;
+    if ((rc = launch_pass(NN4_F64, OP_APPLY, a, P->k64, nullptr, cfg0, 0)) ||
+        (rc = launch_inv_diag(P->k64, P->lk64, P->invd64, P->g64, P->L64.c[0], 0))) {
+      destroy(P);
+      return rc;
+    }
+    if (P->T == NN4_F64) {
+      P->lv[0].k = P->k64;  // same pitch at level 0
+    } else if ((rc = alloc(P, &P->lv[0].k, field_bytes(P->lv[0].g, P->T))) ||
+               (rc = launch_to_inner(P->T, P->k64, P->g64, P->lv[0].k, P->lv[0].g, 0))) {
       destroy(P);
       return rc;
     }

@@ -47,7 +47,7 @@ struct Runner {
   }
 };
 
-template <typename T, typename A, int RY, bool PROD>
+template <typename T, typename A, int RY, bool PROD, bool ISO>
 __device__ __forceinline__ void plane_uv(const T* __restrict__ sx, const T* __restrict__ sk,
                                          const int* rowoff, int cc, int cl, int cr, const A* c,
                                          A* u, A* v, A* centre) {
@@ -68,13 +68,20 @@ __device__ __forceinline__ void plane_uv(const T* __restrict__ sx, const T* __re
   for (int r = 0; r < RY; ++r) {
     const A p00 = r0[r + 1], p10 = r1[r + 1];
     const A p01 = r0[r] + r0[r + 2], p11 = r1[r] + r1[r + 2];
-    v[r] = c[0] * p00 + c[1] * p10 + c[2] * p01 + c[3] * p11;
-    u[r] = c[4] * p00 + c[5] * p10 + c[6] * p01 + c[7] * p11;
+    if (ISO) {  // equal spacings: the face classes c[1], c[2], c[4] vanish
+      v[r] = c[0] * p00 + c[3] * p11;
+      u[r] = c[5] * p10 + c[6] * p01 + c[7] * p11;
+    } else {
+      v[r] = c[0] * p00 + c[1] * p10 + c[2] * p01 + c[3] * p11;
+      u[r] = c[4] * p00 + c[5] * p10 + c[6] * p01 + c[7] * p11;
+    }
     if (centre) centre[r] = p00;
   }
 }
 
-template <typename T, int OP, bool VC, int RY, int TYT, int S>
+// VC: 0 constant coefficient; 1 Eq. k-T with L k on the fly; 2 Eq. k-T with L k (and optionally
+// the inverse diagonal) read pointwise.
+template <typename T, int OP, int VC, bool ISO, int RY, int TYT, int S>
 __global__ void __launch_bounds__(32 * TYT)
     k_pass(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmk,
            const PassArgs a) {
@@ -153,11 +160,13 @@ __global__ void __launch_bounds__(32 * TYT)
     const T* tx_ = reinterpret_cast<const T*>(smem + (s * NF) * TILE_PAD);
     const T* tk_ = reinterpret_cast<const T*>(smem + (s * NF + 1) * TILE_PAD);
     A ux[RY], vx[RY], xcn[RY];
-    plane_uv<T, A, RY, false>(tx_, tx_, rowoff, cc, cl, cr, c, ux, vx, xcn);
+    plane_uv<T, A, RY, false, ISO>(tx_, tx_, rowoff, cc, cl, cr, c, ux, vx, xcn);
     A ukx[RY], vkx[RY], uk[RY], vk[RY], kcn[RY];
-    if (VC) {
-      plane_uv<T, A, RY, true>(tx_, tk_, rowoff, cc, cl, cr, c, ukx, vkx, nullptr);
-      plane_uv<T, A, RY, false>(tk_, tk_, rowoff, cc, cl, cr, c, uk, vk, kcn);
+    if (VC) plane_uv<T, A, RY, true, ISO>(tx_, tk_, rowoff, cc, cl, cr, c, ukx, vkx, nullptr);
+    if (VC == 1) plane_uv<T, A, RY, false, ISO>(tk_, tk_, rowoff, cc, cl, cr, c, uk, vk, kcn);
+    if (VC == 2) {
+#pragma unroll
+      for (int r = 0; r < RY; ++r) kcn[r] = to_acc(tk_[rowoff[r + 1] + cc]);
     }
     if (__syncthreads_or(failed)) {
       failed = true;
@@ -173,17 +182,22 @@ __global__ void __launch_bounds__(32 * TYT)
         if (i < nx && j < ny) {
           const A w = wx * (A)half_count(j, ny) * (A)half_count(kout, nz);
           const A Lx = sx.p1[r] + ux[r];
+          const long long idx = (long long)i + g.pitch * ((long long)j + (long long)ny * kout);
           A Ax, D;
-          if (VC) {
+          if (VC == 1) {
             const A Lkx = skx.p1[r] + ukx[r];
             const A Lk = sk.p1[r] + uk[r];
             Ax = (A)0.5 * w * (Lkx + kc1[r] * Lx - xc1[r] * Lk);
             D = w * (c[0] * kc1[r] - (A)0.5 * Lk);
+          } else if (VC == 2) {
+            const A Lkx = skx.p1[r] + ukx[r];
+            const A hLk = (A)0.5 * to_acc(reinterpret_cast<const T*>(a.lk)[idx]);  // 1/2 (L k), w included
+            Ax = (A)0.5 * w * (Lkx + kc1[r] * Lx) - xc1[r] * hLk;
+            D = w * c[0] * kc1[r] - hLk;
           } else {
             Ax = w * Lx;
             D = w * c[0];
           }
-          const long long idx = (long long)i + g.pitch * ((long long)j + (long long)ny * kout);
           T* out = reinterpret_cast<T*>(a.out);
           if (OP == OP_APPLY) {
             out[idx] = from_acc<T>(Ax);
@@ -200,7 +214,9 @@ __global__ void __launch_bounds__(32 * TYT)
               nrm += (double)xc1[r] * (double)qv;
               dt2 += (double)xc1[r] * (double)bv;
             } else {
-              const A xn = dirn ? xc1[r] : xc1[r] + (A)a.omega * (bv - Ax) / D;
+              const A corr = (VC == 2 && a.invd) ? (bv - Ax) * to_acc(reinterpret_cast<const T*>(a.invd)[idx])
+                                                  : (bv - Ax) / D;
+              const A xn = dirn ? xc1[r] : xc1[r] + (A)a.omega * corr;
               out[idx] = from_acc<T>(xn);
             }
           }
@@ -213,9 +229,11 @@ __global__ void __launch_bounds__(32 * TYT)
       if (VC) {
         skx.p1[r] = skx.p2[r] + vkx[r];
         skx.p2[r] = ukx[r];
+        kc1[r] = kcn[r];
+      }
+      if (VC == 1) {
         sk.p1[r] = sk.p2[r] + vk[r];
         sk.p2[r] = uk[r];
-        kc1[r] = kcn[r];
       }
     }
   }
@@ -231,7 +249,7 @@ __global__ void __launch_bounds__(32 * TYT)
   if (OP == OP_MATVEC && a.dot2 != nullptr) block_sum_atomic(dt2, a.dot2, red);
 }
 
-template <typename T, int OP, bool VC, int RY, int TYT, int S>
+template <typename T, int OP, int VC, bool ISO, int RY, int TYT, int S>
 int launch_t(const PassArgs& a, const CUtensorMap& mx, const CUtensorMap& mk, cudaStream_t st) {
   constexpr int AL = kAlign<T>;
   constexpr int BX = 32 + 2 * AL;
@@ -239,7 +257,7 @@ int launch_t(const PassArgs& a, const CUtensorMap& mx, const CUtensorMap& mk, cu
   constexpr int NF = VC ? 2 : 1;
   constexpr int TILE_PAD = (BX * BY * (int)sizeof(T) + 127) / 128 * 128;
   const size_t smem = (size_t)S * NF * TILE_PAD + S * 8 + 32 * 8;
-  auto kern = k_pass<T, OP, VC, RY, TYT, S>;
+  auto kern = k_pass<T, OP, VC, ISO, RY, TYT, S>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(stencil pass)");
@@ -249,30 +267,40 @@ int launch_t(const PassArgs& a, const CUtensorMap& mx, const CUtensorMap& mk, cu
   return check_cuda(cudaGetLastError(), "stencil pass launch");
 }
 
-template <typename T, int OP, bool VC>
+template <typename T, int OP, int VC, bool ISO>
 int dispatch_cfg(const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx,
                  const CUtensorMap& mk, cudaStream_t st) {
   // The configurations the autotuner chooses from.
-  if (cfg.stages == 3 && cfg.tyt == 4 && cfg.ry == 4) return launch_t<T, OP, VC, 4, 4, 3>(a, mx, mk, st);
-  if (cfg.stages == 3 && cfg.tyt == 8 && cfg.ry == 2) return launch_t<T, OP, VC, 2, 8, 3>(a, mx, mk, st);
-  if (cfg.stages == 3 && cfg.tyt == 4 && cfg.ry == 2) return launch_t<T, OP, VC, 2, 4, 3>(a, mx, mk, st);
-  if (cfg.stages == 4 && cfg.tyt == 4 && cfg.ry == 4) return launch_t<T, OP, VC, 4, 4, 4>(a, mx, mk, st);
-  if (cfg.stages == 2 && cfg.tyt == 2 && cfg.ry == 2) return launch_t<T, OP, VC, 2, 2, 2>(a, mx, mk, st);
+  if (cfg.stages == 3 && cfg.tyt == 4 && cfg.ry == 4) return launch_t<T, OP, VC, ISO, 4, 4, 3>(a, mx, mk, st);
+  if (cfg.stages == 3 && cfg.tyt == 8 && cfg.ry == 2) return launch_t<T, OP, VC, ISO, 2, 8, 3>(a, mx, mk, st);
+  if (cfg.stages == 4 && cfg.tyt == 4 && cfg.ry == 2) return launch_t<T, OP, VC, ISO, 2, 4, 4>(a, mx, mk, st);
   return set_error(NN4_EINVAL, "unsupported stencil pass configuration");
 }
 
-template <typename T>
-int dispatch_op(int op, bool vc, const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx,
+template <typename T, int OP, int VC>
+int dispatch_iso(bool iso, const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx, const CUtensorMap& mk,
+                 cudaStream_t st) {
+  return iso ? dispatch_cfg<T, OP, VC, true>(a, cfg, mx, mk, st) : dispatch_cfg<T, OP, VC, false>(a, cfg, mx, mk, st);
+}
+
+template <typename T, int OP>
+int dispatch_vc(int vc, bool iso, const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx,
                 const CUtensorMap& mk, cudaStream_t st) {
-  switch (op * 2 + (vc ? 1 : 0)) {
-    case OP_APPLY * 2: return dispatch_cfg<T, OP_APPLY, false>(a, cfg, mx, mk, st);
-    case OP_APPLY * 2 + 1: return dispatch_cfg<T, OP_APPLY, true>(a, cfg, mx, mk, st);
-    case OP_RESIDUAL * 2: return dispatch_cfg<T, OP_RESIDUAL, false>(a, cfg, mx, mk, st);
-    case OP_RESIDUAL * 2 + 1: return dispatch_cfg<T, OP_RESIDUAL, true>(a, cfg, mx, mk, st);
-    case OP_JACOBI * 2: return dispatch_cfg<T, OP_JACOBI, false>(a, cfg, mx, mk, st);
-    case OP_JACOBI * 2 + 1: return dispatch_cfg<T, OP_JACOBI, true>(a, cfg, mx, mk, st);
-    case OP_MATVEC * 2: return dispatch_cfg<T, OP_MATVEC, false>(a, cfg, mx, mk, st);
-    case OP_MATVEC * 2 + 1: return dispatch_cfg<T, OP_MATVEC, true>(a, cfg, mx, mk, st);
+  if (vc == 0) return dispatch_iso<T, OP, 0>(iso, a, cfg, mx, mk, st);
+  if (vc == 1) return dispatch_iso<T, OP, 1>(iso, a, cfg, mx, mk, st);
+  if constexpr (sizeof(T) == 8) return dispatch_iso<T, OP, 2>(iso, a, cfg, mx, mk, st);
+  return set_error(NN4_EINVAL, "precomputed L k is supported for FP64 passes only");
+}
+
+template <typename T>
+int dispatch_op(int op, int vc, const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx,
+                const CUtensorMap& mk, cudaStream_t st) {
+  const bool iso = a.L.c[1] == 0.0 && a.L.c[2] == 0.0 && a.L.c[4] == 0.0;
+  switch (op) {
+    case OP_APPLY: return dispatch_vc<T, OP_APPLY>(vc, iso, a, cfg, mx, mk, st);
+    case OP_RESIDUAL: return dispatch_vc<T, OP_RESIDUAL>(vc, iso, a, cfg, mx, mk, st);
+    case OP_JACOBI: return dispatch_vc<T, OP_JACOBI>(vc, iso, a, cfg, mx, mk, st);
+    case OP_MATVEC: return dispatch_vc<T, OP_MATVEC>(vc, iso, a, cfg, mx, mk, st);
   }
   return set_error(NN4_EINVAL, "bad stencil op");
 }
@@ -316,10 +344,11 @@ int launch_pass(nn4_dtype dt, int op, const PassArgs& a, const void* x, const vo
     mk = &tk;
   }
   if (!vc) mk = mx;
+  const int vmode = vc ? (a.lk ? 2 : 1) : 0;
   switch (dt) {
-    case NN4_F64: return dispatch_op<double>(op, vc, a, cfg, *mx, *mk, s);
-    case NN4_F32: return dispatch_op<float>(op, vc, a, cfg, *mx, *mk, s);
-    case NN4_BF16: return dispatch_op<bf16>(op, vc, a, cfg, *mx, *mk, s);
+    case NN4_F64: return dispatch_op<double>(op, vmode, a, cfg, *mx, *mk, s);
+    case NN4_F32: return dispatch_op<float>(op, vmode, a, cfg, *mx, *mk, s);
+    case NN4_BF16: return dispatch_op<bf16>(op, vmode, a, cfg, *mx, *mk, s);
   }
   return set_error(NN4_EINVAL, "bad dtype");
 }
