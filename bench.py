@@ -151,6 +151,7 @@ def config_dict(args):
                         "1000:1 seeded sphere R=0.2 smoothed over 2 cells, zero-derivative walls, "
                         "f ~ N(0,1) zero-mean, x0 = 0, to 1e-8 relative residual",
             "inner": args.inner, "outer": "fcg (FP64)", "inner_cycles": args.m,
+            "inner_krylov": args.krylov,
             "coarse_operators": "Galerkin", "smoother": "weighted Jacobi omega=2/3, 1 sweep per level",
             "l2": "inputs larger than L2 (b, x, k: 3 x 144 MB FP64 plus the hierarchy)"}
 
@@ -162,7 +163,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--inner", default="bf16", choices=["bf16", "f32"])
-    ap.add_argument("--m", type=int, default=2, help="V-cycles per outer iteration")
+    ap.add_argument("--m", type=int, default=2, help="V-cycles per outer iteration (or per inner iteration)")
+    ap.add_argument("--krylov", type=int, default=0, help="inner FP32 flexible-CG iterations (0: none)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--ref-n", type=int, default=65)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
@@ -198,7 +200,8 @@ def main():
     B = nn4.to_field(b_host, G)
     X = nn4.field(G)
     inner = nn4.BF16 if args.inner == "bf16" else nn4.F32
-    plan = nn4.Plan(G, K, inner=inner, inner_cycles=args.m, outer=nn4.OUTER_FCG, check_every=2)
+    plan = nn4.Plan(G, K, inner=inner, inner_cycles=args.m, outer=nn4.OUTER_FCG, check_every=2,
+                    inner_krylov=args.krylov)
     stream = torch.cuda.current_stream()
 
     def solve(p, x):
@@ -283,7 +286,7 @@ def main():
 
     # per-kernel durations from an eagerly launched, event-timed solve of the same plan setup
     prof_plan = nn4.Plan(G, K, inner=inner, inner_cycles=args.m, outer=nn4.OUTER_FCG, check_every=2,
-                         profile=True)
+                         profile=True, inner_krylov=args.krylov)
     solve(prof_plan, X)
     prof_plan.profile()
     solve(prof_plan, X)

@@ -119,10 +119,18 @@ typedef struct {
   int32_t check_every;   /* read the residual norm back every this many outer iterations (>=1) */
   int32_t profile;       /* 1: launch eagerly and time every kernel with CUDA events (see
                             nn4_plan_profile); for measurement only */
+  int32_t inner_krylov;  /* 0: the preconditioner is inner_cycles V-cycles.  n > 0: it is n
+                            iterations of flexible CG in FP32 vectors on A e = r, each
+                            preconditioned by inner_cycles V-cycles (mixed precision only) */
+  int32_t coarse_tail;   /* 1: run every level at or below 6000 nodes in one single-CTA launch
+                            (same arithmetic as the per-level kernels); 0: one launch per step */
+  int32_t autotune;      /* 1: time the compiled tile shapes, pipeline depths and z-march depths
+                            of every stencil pass at plan creation and keep the fastest (cached
+                            per process by grid size); 0: fixed defaults */
 } nn4_plan_opts;
 
 /* Fills o with the defaults: F64, 1 cycle, NN4_OUTER_CYCLES, omega 2/3, graphs on, check 1,
- * profile off. */
+ * profile off, no inner Krylov loop, coarse tail on, autotuning on. */
 void nn4_plan_opts_default(nn4_plan_opts* o);
 
 typedef struct nn4_plan_s* nn4_plan;

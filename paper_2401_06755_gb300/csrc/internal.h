@@ -47,6 +47,7 @@ struct PassArgs {
 
 // Stencil pass launch configuration (chosen by the autotuner or by default).
 struct PassCfg {
+  int wx;      // warps along x (tile width 32 wx)
   int ry;      // outputs per thread along y
   int tyt;     // threads along y (x is always one warp of 32)
   int stages;  // TMA pipeline depth (planes in flight)
@@ -65,13 +66,21 @@ size_t dtype_size(nn4_dtype dt);
 unsigned int stencil_error_word();
 
 // ---------------------------------------------------------------- launchers
-// stencil.cu: constant coefficient (k == nullptr) or Eq. k-T (k given).  x and k are read with
-// TMA (their tensor maps are built here unless maps are given).
+// Tensor maps of one stencil pass: haloed tiles of x and k, pointwise tiles of b, L k, 1/diag.
+struct PassMaps {
+  CUtensorMap x, k, b, lk, invd;
+};
+
+// stencil.cu: constant coefficient (k == nullptr) or Eq. k-T (k given).  Every input is read with
+// TMA; the maps are built here unless `maps` is given (built with make_pass_maps for this cfg).
 int launch_pass(nn4_dtype dt, int op, const PassArgs& a, const void* x, const void* k,
-                const PassCfg& cfg, cudaStream_t s, const CUtensorMap* mx = nullptr,
-                const CUtensorMap* mk = nullptr);
+                const PassCfg& cfg, cudaStream_t s, const PassMaps* maps = nullptr);
+bool make_pass_maps(PassMaps* m, nn4_dtype dt, const PassArgs& a, const PassCfg& cfg, const void* x, const void* k);
 PassCfg default_pass_cfg(nn4_dtype dt, bool vc, const LevelGeom& g);
+int num_pass_cfgs();
+PassCfg pass_cfg_candidate(int index, const LevelGeom& g, int zchunk);
 int pass_box(nn4_dtype dt, const PassCfg& cfg, int* box_x, int* box_y);
+int pass_point_box(const PassCfg& cfg, int* box_x, int* box_y);
 
 // transfer.cu
 int launch_restrict(nn4_dtype dt, const void* rf, const LevelGeom& gf, void* rc,
@@ -87,5 +96,31 @@ int launch_prolong_base(nn4_dtype dt, const void* ec, const LevelGeom& gc, void*
 // e += Ainv r at free nodes and other nodes are left alone.
 int launch_coarse_solve(nn4_dtype dt, const double* ainv, const int* free_idx, int nfree,
                         const void* r, void* e, const LevelGeom& g, int accumulate, cudaStream_t s);
+
+// tail.cu: the coarse levels of a V-cycle in one single-CTA launch.  Level 0 of the tail is the
+// entry level (its r holds the restricted residual on entry, its e the correction on exit);
+// the last level is the coarsest (dense solve with ainv over free_idx).
+constexpr int kMaxTail = 8;
+constexpr int kTailNodes = 6000;  // levels at or below this many nodes join the tail
+
+struct TailLevel {
+  LevelGeom g;
+  Coef8 L;          // constant-coefficient stencil (used when a27 is NULL)
+  void* r;
+  void* e;
+  void* t;
+  const void* a27;  // Galerkin coefficients or NULL
+};
+
+struct TailArgs {
+  int nlev;
+  TailLevel lv[kMaxTail];
+  const double* ainv;
+  const int* free_idx;
+  int nfree;
+  double omega;
+};
+
+int launch_tail(nn4_dtype dt, const TailArgs& a, cudaStream_t s);
 
 }  // namespace nn4

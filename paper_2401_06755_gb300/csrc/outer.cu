@@ -12,7 +12,7 @@ namespace {
 #define NN4_FOR_NODES(G)                                                                    \
   for (long long row = blockIdx.x * (long long)blockDim.y + threadIdx.y;                     \
        row < (long long)(G).ny * (G).nz; row += (long long)gridDim.x * blockDim.y)           \
-    for (int i = threadIdx.x; i < (G).nx; i += blockDim.x)
+    _Pragma("unroll 4") for (int i = threadIdx.x; i < (G).nx; i += blockDim.x)
 
 __device__ __forceinline__ bool dirichlet_row(const LevelGeom& g, long long row, int i) {
   const int j = (int)(row % g.ny), k = (int)(row / g.ny);
@@ -44,42 +44,42 @@ __global__ void k_norm_masked(const double* __restrict__ v, LevelGeom g, double*
   block_sum_atomic(s, out, red);
 }
 
-// out += sum z_i * q_i (z in the inner type, q FP64)
-template <typename T>
-__global__ void k_dot_zq(const T* __restrict__ z, LevelGeom gT, const double* __restrict__ q, LevelGeom g64,
+// out += sum z_i * q_i (z of type TZ, q of type V)
+template <typename TZ, typename V>
+__global__ void k_dot_zq(const TZ* __restrict__ z, LevelGeom gz, const V* __restrict__ q, LevelGeom gv,
                          double* out) {
   __shared__ double red[32];
   double s = 0.0;
-  NN4_FOR_NODES(g64) { s += (double)to_acc(z[row * gT.pitch + i]) * q[row * g64.pitch + i]; }
+  NN4_FOR_NODES(gv) { s += (double)to_acc(z[row * gz.pitch + i]) * (double)q[row * gv.pitch + i]; }
   block_sum_atomic(s, out, red);
 }
 
 // p = z - beta p_old with beta = zq / pq_old
-template <typename T>
-__global__ void k_new_direction(const T* __restrict__ z, LevelGeom gT, const double* __restrict__ p_old,
-                                double* __restrict__ p, LevelGeom g64, const double* zq, const double* pq_old) {
-  const double beta = *zq / *pq_old;
-  NN4_FOR_NODES(g64) {
-    const long long o = row * g64.pitch + i;
-    p[o] = (double)to_acc(z[row * gT.pitch + i]) - beta * p_old[o];
+template <typename TZ, typename V>
+__global__ void k_new_direction(const TZ* __restrict__ z, LevelGeom gz, const V* __restrict__ p_old,
+                                V* __restrict__ p, LevelGeom gv, const double* zq, const double* pq_old) {
+  const V beta = (V)(*zq / *pq_old);
+  NN4_FOR_NODES(gv) {
+    const long long o = row * gv.pitch + i;
+    p[o] = (V)to_acc(z[row * gz.pitch + i]) - beta * p_old[o];
   }
 }
 
-// alpha = pr / pq; x += alpha p; r -= alpha q; rT = r; norm += r^2 (free nodes)
-template <typename T>
-__global__ void k_fcg_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                             const double* __restrict__ q, LevelGeom g64, T* __restrict__ rT, LevelGeom gT,
+// alpha = pr / pq; x += alpha p; r -= alpha q; rT = r (if rT); norm += r^2
+template <typename V, typename TR>
+__global__ void k_fcg_update(V* __restrict__ x, V* __restrict__ r, const V* __restrict__ p,
+                             const V* __restrict__ q, LevelGeom gv, TR* __restrict__ rT, LevelGeom gT,
                              const double* pr, const double* pq, double* norm2) {
   __shared__ double red[32];
-  const double alpha = *pr / *pq;
+  const V alpha = (V)(*pr / *pq);
   double s = 0.0;
-  NN4_FOR_NODES(g64) {
-    const long long o = row * g64.pitch + i;
+  NN4_FOR_NODES(gv) {
+    const long long o = row * gv.pitch + i;
     x[o] += alpha * p[o];
-    const double rn = r[o] - alpha * q[o];
+    const V rn = r[o] - alpha * q[o];
     r[o] = rn;
-    if (rT) rT[row * gT.pitch + i] = from_acc<T>(rn);
-    s += rn * rn;
+    if (rT) rT[row * gT.pitch + i] = from_acc<TR>(rn);
+    s += (double)rn * (double)rn;
   }
   block_sum_atomic(s, norm2, red);
 }
@@ -114,22 +114,29 @@ int to_inner_t(const double* r, const LevelGeom& g64, void* rT, const LevelGeom&
   k_to_inner<T><<<pw_grid(g64), kPwBlock, 0, s>>>(r, g64, static_cast<T*>(rT), gT);
   return check_cuda(cudaGetLastError(), "to inner");
 }
-template <typename T>
-int dot_zq_t(const void* z, const LevelGeom& gT, const double* q, const LevelGeom& g64, double* out, cudaStream_t s) {
-  k_dot_zq<T><<<pw_grid(g64), kPwBlock, 0, s>>>(static_cast<const T*>(z), gT, q, g64, out);
+template <typename TZ, typename V>
+int dot_zq_t(const void* z, const LevelGeom& gz, const void* q, const LevelGeom& gv, double* out, cudaStream_t s) {
+  k_dot_zq<TZ, V><<<pw_grid(gv), kPwBlock, 0, s>>>(static_cast<const TZ*>(z), gz, static_cast<const V*>(q), gv, out);
   return check_cuda(cudaGetLastError(), "dot");
 }
-template <typename T>
-int new_direction_t(const void* z, const LevelGeom& gT, const double* p_old, double* p, const LevelGeom& g64,
+template <typename TZ, typename V>
+int new_direction_t(const void* z, const LevelGeom& gz, const void* p_old, void* p, const LevelGeom& gv,
                     const double* zq, const double* pq_old, cudaStream_t s) {
-  k_new_direction<T><<<pw_grid(g64), kPwBlock, 0, s>>>(static_cast<const T*>(z), gT, p_old, p, g64, zq, pq_old);
+  k_new_direction<TZ, V><<<pw_grid(gv), kPwBlock, 0, s>>>(static_cast<const TZ*>(z), gz, static_cast<const V*>(p_old),
+                                                           static_cast<V*>(p), gv, zq, pq_old);
   return check_cuda(cudaGetLastError(), "new direction");
 }
-template <typename T>
-int fcg_update_t(double* x, double* r, const double* p, const double* q, const LevelGeom& g64, void* rT,
+template <typename V, typename TR>
+int fcg_update_t(void* x, void* r, const void* p, const void* q, const LevelGeom& gv, void* rT,
                  const LevelGeom& gT, const double* pr, const double* pq, double* norm2, cudaStream_t s) {
-  k_fcg_update<T><<<pw_grid(g64), kPwBlock, 0, s>>>(x, r, p, q, g64, static_cast<T*>(rT), gT, pr, pq, norm2);
+  k_fcg_update<V, TR><<<pw_grid(gv), kPwBlock, 0, s>>>(static_cast<V*>(x), static_cast<V*>(r), static_cast<const V*>(p),
+                                                        static_cast<const V*>(q), gv, static_cast<TR*>(rT), gT, pr, pq,
+                                                        norm2);
   return check_cuda(cudaGetLastError(), "fcg update");
+}
+template <typename TS, typename TD>
+__global__ void k_convert(const TS* __restrict__ a, LevelGeom ga, TD* __restrict__ b, LevelGeom gb) {
+  NN4_FOR_NODES(ga) { b[row * gb.pitch + i] = from_acc<TD>(to_acc(a[row * ga.pitch + i])); }
 }
 
 }  // namespace
@@ -160,18 +167,76 @@ int launch_norm_masked(const double* v, const LevelGeom& g, double* out, cudaStr
   k_norm_masked<<<pw_grid(g), kPwBlock, 0, s>>>(v, g, out);
   return check_cuda(cudaGetLastError(), "norm");
 }
+#define NN4_DISPATCH2(da, db, call)                                                       \
+  switch (da * 3 + db) {                                                                  \
+    case NN4_F64 * 3 + NN4_F64: { using A1 = double; using B1 = double; return call; }  \
+    case NN4_F32 * 3 + NN4_F64: { using A1 = float; using B1 = double; return call; }   \
+    case NN4_BF16 * 3 + NN4_F64: { using A1 = bf16; using B1 = double; return call; }   \
+    case NN4_F64 * 3 + NN4_F32: { using A1 = double; using B1 = float; return call; }   \
+    case NN4_F32 * 3 + NN4_F32: { using A1 = float; using B1 = float; return call; }    \
+    case NN4_BF16 * 3 + NN4_F32: { using A1 = bf16; using B1 = float; return call; }    \
+  }                                                                                       \
+  return set_error(NN4_EINVAL, "unsupported type pair");
+
+int launch_dot(nn4_dtype tz, const void* z, const LevelGeom& gz, nn4_dtype tv, const void* q, const LevelGeom& gv,
+               double* out, cudaStream_t s) {
+  NN4_DISPATCH2(tz, tv, (dot_zq_t<A1, B1>(z, gz, q, gv, out, s)))
+}
+int launch_direction(nn4_dtype tz, const void* z, const LevelGeom& gz, nn4_dtype tv, const void* p_old, void* p,
+                     const LevelGeom& gv, const double* zq, const double* pq_old, cudaStream_t s) {
+  NN4_DISPATCH2(tz, tv, (new_direction_t<A1, B1>(z, gz, p_old, p, gv, zq, pq_old, s)))
+}
+int launch_update(nn4_dtype tv, void* x, void* r, const void* p, const void* q, const LevelGeom& gv, nn4_dtype tr,
+                  void* rT, const LevelGeom& gT, const double* pr, const double* pq, double* norm2, cudaStream_t s) {
+  if (tv == NN4_F64) {
+    switch (tr) {
+      case NN4_F64: return fcg_update_t<double, double>(x, r, p, q, gv, rT, gT, pr, pq, norm2, s);
+      case NN4_F32: return fcg_update_t<double, float>(x, r, p, q, gv, rT, gT, pr, pq, norm2, s);
+      case NN4_BF16: return fcg_update_t<double, bf16>(x, r, p, q, gv, rT, gT, pr, pq, norm2, s);
+    }
+  } else if (tv == NN4_F32) {
+    switch (tr) {
+      case NN4_F64: return set_error(NN4_EINVAL, "bad type pair");
+      case NN4_F32: return fcg_update_t<float, float>(x, r, p, q, gv, rT, gT, pr, pq, norm2, s);
+      case NN4_BF16: return fcg_update_t<float, bf16>(x, r, p, q, gv, rT, gT, pr, pq, norm2, s);
+    }
+  }
+  return set_error(NN4_EINVAL, "unsupported type pair");
+}
+int launch_convert(nn4_dtype ta, const void* a, const LevelGeom& ga, nn4_dtype tb, void* b, const LevelGeom& gb,
+                   cudaStream_t s) {
+  switch (ta * 3 + tb) {
+    case NN4_F64 * 3 + NN4_F32:
+      k_convert<double, float><<<pw_grid(ga), kPwBlock, 0, s>>>(static_cast<const double*>(a), ga, static_cast<float*>(b), gb);
+      break;
+    case NN4_F64 * 3 + NN4_BF16:
+      k_convert<double, bf16><<<pw_grid(ga), kPwBlock, 0, s>>>(static_cast<const double*>(a), ga, static_cast<bf16*>(b), gb);
+      break;
+    case NN4_F32 * 3 + NN4_BF16:
+      k_convert<float, bf16><<<pw_grid(ga), kPwBlock, 0, s>>>(static_cast<const float*>(a), ga, static_cast<bf16*>(b), gb);
+      break;
+    case NN4_F32 * 3 + NN4_F64:
+      k_convert<float, double><<<pw_grid(ga), kPwBlock, 0, s>>>(static_cast<const float*>(a), ga, static_cast<double*>(b), gb);
+      break;
+    default:
+      return set_error(NN4_EINVAL, "unsupported conversion");
+  }
+  return check_cuda(cudaGetLastError(), "convert");
+}
+
+// FP64-vector forms used by the outer loop
 int launch_dot_zq(nn4_dtype dt, const void* z, const LevelGeom& gT, const double* q, const LevelGeom& g64,
                   double* out, cudaStream_t s) {
-  NN4_DISPATCH(dt, dot_zq_t<T>(z, gT, q, g64, out, s))
+  return launch_dot(dt, z, gT, NN4_F64, q, g64, out, s);
 }
 int launch_new_direction(nn4_dtype dt, const void* z, const LevelGeom& gT, const double* p_old, double* p,
                          const LevelGeom& g64, const double* zq, const double* pq_old, cudaStream_t s) {
-  NN4_DISPATCH(dt, new_direction_t<T>(z, gT, p_old, p, g64, zq, pq_old, s))
+  return launch_direction(dt, z, gT, NN4_F64, p_old, p, g64, zq, pq_old, s);
 }
 int launch_fcg_update(nn4_dtype dt, double* x, double* r, const double* p, const double* q, const LevelGeom& g64,
                       void* rT, const LevelGeom& gT, const double* pr, const double* pq, double* norm2,
                       cudaStream_t s) {
-  NN4_DISPATCH(dt, fcg_update_t<T>(x, r, p, q, g64, rT, gT, pr, pq, norm2, s))
+  return launch_update(NN4_F64, x, r, p, q, g64, dt, rT, gT, pr, pq, norm2, s);
 }
 
 }  // namespace nn4

@@ -27,4 +27,14 @@ int launch_fcg_update(nn4_dtype dt, double* x, double* r, const double* p, const
                       void* rT, const LevelGeom& gT, const double* pr, const double* pq, double* norm2,
                       cudaStream_t s);
 
+// Generic-precision forms (vectors V in FP64 or FP32; z / rT in any storage type).
+int launch_dot(nn4_dtype tz, const void* z, const LevelGeom& gz, nn4_dtype tv, const void* q, const LevelGeom& gv,
+               double* out, cudaStream_t s);
+int launch_direction(nn4_dtype tz, const void* z, const LevelGeom& gz, nn4_dtype tv, const void* p_old, void* p,
+                     const LevelGeom& gv, const double* zq, const double* pq_old, cudaStream_t s);
+int launch_update(nn4_dtype tv, void* x, void* r, const void* p, const void* q, const LevelGeom& gv, nn4_dtype tr,
+                  void* rT, const LevelGeom& gT, const double* pr, const double* pq, double* norm2, cudaStream_t s);
+int launch_convert(nn4_dtype ta, const void* a, const LevelGeom& ga, nn4_dtype tb, void* b, const LevelGeom& gb,
+                   cudaStream_t s);
+
 }  // namespace nn4

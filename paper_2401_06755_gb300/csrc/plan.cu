@@ -8,6 +8,9 @@
 // CUDA graph (captured at the first solve), so a solve is a few graph launches plus one
 // residual-norm readback per `check_every` iterations.
 #include <cmath>
+#include <mutex>
+#include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -31,10 +34,9 @@ struct Level {
   void* r = nullptr;  // right-hand side of this level
   void* e = nullptr;  // correction (output of the Jacobi sweep)
   void* t = nullptr;  // prolongated correction / fine residual (input of the Jacobi sweep)
-  CUtensorMap tm_t{}, tm_e{};
+  PassMaps m_jac{}, m_res{};  // Jacobi (x = t, b = r) and residual (x = e, b = r) passes
   void* a27 = nullptr;  // Galerkin coefficients (coefficient field, levels >= 1)
   void* k = nullptr;    // coefficient field in the inner type (level 0)
-  CUtensorMap tm_k{};
 };
 
 }  // namespace
@@ -56,13 +58,21 @@ struct PlanImpl {
   double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *p64[2] = {nullptr, nullptr},
          *q64[2] = {nullptr, nullptr}, *k64 = nullptr;
   double *lk64 = nullptr, *invd64 = nullptr;  // L k and 1/diag(A) for Eq. k-T (FP64)
-  CUtensorMap tm_x64{}, tm_p64[2]{}, tm_k64{};
+  // inner flexible CG in FP32 vectors (opts.inner_krylov > 0): solution y, residual r, directions
+  // p[2], q[2], coefficient k (FP32), all at the FP32 level-0 pitch
+  LevelGeom g32;
+  PassCfg cfg32;
+  float *yi = nullptr, *ri = nullptr, *pi[2] = {nullptr, nullptr}, *qi[2] = {nullptr, nullptr}, *k32 = nullptr;
+  PassMaps m_mat32[2]{};
+  PassMaps m_res64{}, m_mat64[2]{};
   // device scalars: [0] ||r||^2 (current), [1] ||b||^2, [2] z.q, [3..4] p.q by parity,
-  // [5..6] p.r by parity; then the per-iteration history of ||r||^2
+  // [5..6] p.r by parity; inner loop: [8] z.q, [9..10] p.q, [11..12] p.r, [13] ||r||^2;
+  // [15] the constant 1.0.  Then the per-iteration history of ||r||^2
   double* scal = nullptr;
   double* hist = nullptr;
   int hist_cap = 0;
   double* host_hist = nullptr;  // pinned
+  int tail_start = -1;  // first level handled by the single-launch coarse tail (-1: none)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int64_t graph_kernels[2] = {0, 0};
   cudaStream_t graph_stream = nullptr;
@@ -298,11 +308,13 @@ int build_coarsest(PlanImpl* P, const std::vector<double>& dense_all) {
 struct Fine {
   const void* r;
   void* e;
-  const CUtensorMap* tm_e;
+  const PassMaps* res_maps;  // residual pass on (e, r); NULL: built per launch
+  const PassMaps* jac_maps;  // level-0 Jacobi pass (t, r); NULL: built per launch
 };
 
-int run_pass(PlanImpl* P, int l, int op, const void* x, const CUtensorMap* mx, const void* b, void* out,
-             cudaStream_t s, double* norm2 = nullptr) {
+// Level-l residual / Jacobi pass.  Level 0 with a coefficient field uses k (and, for FP64
+// hierarchies, the precomputed L k and inverse diagonal); Galerkin levels use their 27 arrays.
+PassArgs level_args(PlanImpl* P, int l, const void* b, void* out) {
   Level& L = P->lv[l];
   PassArgs a{};
   a.g = L.g;
@@ -310,19 +322,25 @@ int run_pass(PlanImpl* P, int l, int op, const void* x, const CUtensorMap* mx, c
   a.omega = P->o.omega;
   a.b = b;
   a.out = out;
-  a.norm2 = norm2;
   a.zchunk = L.cfg.zchunk;
+  if (P->vc && l == 0 && P->T == NN4_F64) {
+    a.lk = P->lk64;
+    a.invd = P->invd64;
+  }
+  return a;
+}
+
+int run_pass(PlanImpl* P, int l, int op, const void* x, const PassMaps* maps, const void* b, void* out,
+             cudaStream_t s, double* norm2 = nullptr) {
+  Level& L = P->lv[l];
+  PassArgs a = level_args(P, l, b, out);
+  a.norm2 = norm2;
   if (P->vc && l > 0)
     return K(P, std::string("pass27:") + opname(op) + ":" + lvl(l), s,
              [&] { return launch_pass27(P->T, op, a, x, L.a27, s); });
   const bool vc0 = P->vc && l == 0;
-  if (vc0 && P->T == NN4_F64) {
-    a.lk = P->lk64;
-    a.invd = P->invd64;
-  }
-  return K(P, std::string("pass:") + opname(op) + ":" + lvl(l), s, [&] {
-    return launch_pass(P->T, op, a, x, vc0 ? L.k : nullptr, L.cfg, s, mx, vc0 ? &L.tm_k : nullptr);
-  });
+  return K(P, std::string("pass:") + opname(op) + ":" + lvl(l), s,
+           [&] { return launch_pass(P->T, op, a, x, vc0 ? L.k : nullptr, L.cfg, s, maps); });
 }
 
 int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
@@ -333,44 +351,65 @@ int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
   if (nl == 1) {  // the fine grid is the coarsest: e += A^-1 (r - A e)
     if (first)
       return K(P, "coarsest", s, [&] { return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, F.r, F.e, L0.g, 0, s); });
-    if ((rc = run_pass(P, 0, OP_RESIDUAL, F.e, F.tm_e, F.r, L0.t, s))) return rc;
+    if ((rc = run_pass(P, 0, OP_RESIDUAL, F.e, F.res_maps, F.r, L0.t, s))) return rc;
     return K(P, "coarsest", s, [&] { return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, L0.t, F.e, L0.g, 1, s); });
   }
   // down: fine residual, then restriction to the coarsest level
   const void* r0 = F.r;
   if (!first) {
-    if ((rc = run_pass(P, 0, OP_RESIDUAL, F.e, F.tm_e, F.r, L0.t, s))) return rc;
+    if ((rc = run_pass(P, 0, OP_RESIDUAL, F.e, F.res_maps, F.r, L0.t, s))) return rc;
     r0 = L0.t;
   }
   if ((rc = K(P, "restrict:L0", s, [&] { return launch_restrict(T, r0, L0.g, P->lv[1].r, P->lv[1].g, s); })))
     return rc;
-  for (int l = 1; l + 1 < nl; ++l)
+  const int ts = P->tail_start > 0 ? P->tail_start : nl;  // levels >= ts run in the tail kernel
+  for (int l = 1; l + 1 < nl && l < ts; ++l)
     if ((rc = K(P, "restrict:" + lvl(l), s,
                 [&] { return launch_restrict(T, P->lv[l].r, P->lv[l].g, P->lv[l + 1].r, P->lv[l + 1].g, s); })))
       return rc;
-  Level& C = P->lv[nl - 1];
-  if ((rc = K(P, "coarsest", s,
-              [&] { return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, C.r, C.e, C.g, 0, s); })))
-    return rc;
-  // up: prolongation then one Jacobi sweep per level
-  for (int l = nl - 2; l >= 1; --l) {
+  if (ts < nl) {
+    TailArgs ta{};
+    ta.nlev = nl - ts;
+    for (int l = ts; l < nl; ++l) {
+      Level& L = P->lv[l];
+      TailLevel& t = ta.lv[l - ts];
+      t.g = L.g;
+      t.L = L.L;
+      t.r = L.r;
+      t.e = L.e;
+      t.t = L.t;
+      t.a27 = P->vc ? L.a27 : nullptr;
+    }
+    ta.ainv = P->ainv;
+    ta.free_idx = P->free_idx;
+    ta.nfree = P->nfree;
+    ta.omega = P->o.omega;
+    if ((rc = K(P, "coarse_tail", s, [&] { return launch_tail(T, ta, s); }))) return rc;
+  } else {
+    Level& C = P->lv[nl - 1];
+    if ((rc = K(P, "coarsest", s,
+                [&] { return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, C.r, C.e, C.g, 0, s); })))
+      return rc;
+  }
+  // up: prolongation then one Jacobi sweep per level above the tail
+  for (int l = std::min(ts, nl - 1) - 1; l >= 1; --l) {
     Level& L = P->lv[l];
     if ((rc = K(P, "prolong:" + lvl(l), s,
                 [&] { return launch_prolong_base(T, P->lv[l + 1].e, P->lv[l + 1].g, L.t, nullptr, L.g, s); })))
       return rc;
-    if ((rc = run_pass(P, l, OP_JACOBI, L.t, &L.tm_t, L.r, L.e, s))) return rc;
+    if ((rc = run_pass(P, l, OP_JACOBI, L.t, &L.m_jac, L.r, L.e, s))) return rc;
   }
   if ((rc = K(P, "prolong:L0", s, [&] {
          return launch_prolong_base(T, P->lv[1].e, P->lv[1].g, L0.t, first ? nullptr : F.e, L0.g, s);
        })))
     return rc;
-  return run_pass(P, 0, OP_JACOBI, L0.t, &L0.tm_t, F.r, F.e, s);
+  return run_pass(P, 0, OP_JACOBI, L0.t, F.jac_maps, F.r, F.e, s);
 }
 
 // ---------------------------------------------------------------- outer iterations
 int inner_solve(PlanImpl* P, cudaStream_t s) {
   Level& L0 = P->lv[0];
-  Fine F{L0.r, L0.e, &L0.tm_e};
+  Fine F{L0.r, L0.e, &L0.m_res, &L0.m_jac};
   int rc;
   for (int c = 0; c < P->o.inner_cycles; ++c)
     if ((rc = vcycle_impl(P, F, c == 0, s))) return rc;
@@ -386,42 +425,126 @@ int outer_residual(PlanImpl* P, cudaStream_t s, double* norm2) {
   a.out = P->r64;
   a.norm2 = norm2;
   a.zchunk = P->cfg64.zchunk;
-  a.lk = P->lk64;
+  a.lk = P->vc ? P->lk64 : nullptr;
   int rc;
   if ((rc = check_cuda(cudaMemsetAsync(norm2, 0, sizeof(double), s), "zero norm"))) return rc;
   return K(P, "pass64:residual", s, [&] {
-    return launch_pass(NN4_F64, OP_RESIDUAL, a, P->x64, P->vc ? P->k64 : nullptr, P->cfg64, s, &P->tm_x64,
-                       P->vc ? &P->tm_k64 : nullptr);
+    return launch_pass(NN4_F64, OP_RESIDUAL, a, P->x64, P->vc ? P->k64 : nullptr, P->cfg64, s, &P->m_res64);
   });
 }
 
-// One defect-correction iteration: rT = r; e = cycles(rT); x += e; r = b - A x (norm -> scal[0]).
-int iteration_cycles(PlanImpl* P, cudaStream_t s) {
+// The preconditioned vector z of the outer loop.
+struct ZRef {
+  nn4_dtype t;
+  const void* p;
+  LevelGeom g;
+};
+
+// Where the outer loop puts the residual for the preconditioner (rT) and its type.
+void residual_sink(PlanImpl* P, nn4_dtype* t, void** p, LevelGeom* g) {
+  if (P->o.inner_krylov > 0) {
+    *t = NN4_F32;
+    *p = P->ri;
+    *g = P->g32;
+  } else {
+    *t = P->T;
+    *p = P->T == NN4_F64 ? nullptr : P->lv[0].r;  // FP64: level 0 reads r64 directly
+    *g = P->lv[0].g;
+  }
+}
+
+// Inner flexible CG (FP32 vectors) on A y = ri from y = 0, `inner_krylov` iterations, each
+// preconditioned by the V-cycles; ri holds the outer residual on entry.
+int inner_krylov(PlanImpl* P, cudaStream_t s) {
   Level& L0 = P->lv[0];
   int rc;
-  if (P->T != NN4_F64 &&
-      (rc = K(P, "pointwise:to_inner", s, [&] { return launch_to_inner(P->T, P->r64, P->g64, L0.r, L0.g, s); })))
+  const size_t fb = field_bytes(P->g32, NN4_F32);
+  if ((rc = check_cuda(cudaMemsetAsync(P->yi, 0, fb, s), "zero y")) ||
+      (rc = check_cuda(cudaMemsetAsync(P->pi[1], 0, fb, s), "zero p")) ||
+      (rc = check_cuda(cudaMemsetAsync(P->qi[1], 0, fb, s), "zero q")) ||
+      (rc = check_cuda(cudaMemcpyAsync(P->scal + 10, P->scal + 15, sizeof(double), cudaMemcpyDeviceToDevice, s), "pq")))
     return rc;
-  if ((rc = inner_solve(P, s))) return rc;
-  if ((rc = K(P, "pointwise:add_correction", s,
-              [&] { return launch_add_correction(P->T, P->x64, P->g64, L0.e, L0.g, s); })))
+  if (P->T == NN4_BF16 &&
+      (rc = K(P, "pointwise:convert", s, [&] { return launch_convert(NN4_F32, P->ri, P->g32, NN4_BF16, L0.r, L0.g, s); })))
+    return rc;
+  for (int j = 0; j < P->o.inner_krylov; ++j) {
+    const int par = j & 1, old = 1 - par;
+    if ((rc = inner_solve(P, s))) return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(P->scal + 8, 0, sizeof(double), s), "zero zq"))) return rc;
+    if ((rc = K(P, "inner:dot", s,
+                [&] { return launch_dot(P->T, L0.e, L0.g, NN4_F32, P->qi[old], P->g32, P->scal + 8, s); })))
+      return rc;
+    if ((rc = K(P, "inner:direction", s, [&] {
+           return launch_direction(P->T, L0.e, L0.g, NN4_F32, P->pi[old], P->pi[par], P->g32, P->scal + 8,
+                                   P->scal + 9 + old, s);
+         })))
+      return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(P->scal + 9 + par, 0, sizeof(double), s), "zero")) ||
+        (rc = check_cuda(cudaMemsetAsync(P->scal + 11 + par, 0, sizeof(double), s), "zero")))
+      return rc;
+    PassArgs a{};
+    a.g = P->g32;
+    a.L = L0.L;
+    a.b = P->ri;
+    a.out = P->qi[par];
+    a.norm2 = P->scal + 9 + par;
+    a.dot2 = P->scal + 11 + par;
+    a.zchunk = P->cfg32.zchunk;
+    if ((rc = K(P, "inner:matvec", s, [&] {
+           return launch_pass(NN4_F32, OP_MATVEC, a, P->pi[par], P->vc ? P->k32 : nullptr, P->cfg32, s,
+                              &P->m_mat32[par]);
+         })))
+      return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(P->scal + 13, 0, sizeof(double), s), "zero"))) return rc;
+    if ((rc = K(P, "inner:update", s, [&] {
+           return launch_update(NN4_F32, P->yi, P->ri, P->pi[par], P->qi[par], P->g32, P->T,
+                                P->T == NN4_BF16 ? L0.r : nullptr, L0.g, P->scal + 11 + par, P->scal + 9 + par,
+                                P->scal + 13, s);
+         })))
+      return rc;
+  }
+  return NN4_OK;
+}
+
+// Applies the preconditioner to the residual left by the outer loop in its sink.
+int precondition(PlanImpl* P, cudaStream_t s, ZRef* z) {
+  if (P->o.inner_krylov > 0) {
+    *z = ZRef{NN4_F32, P->yi, P->g32};
+    return inner_krylov(P, s);
+  }
+  *z = ZRef{P->T, P->lv[0].e, P->lv[0].g};
+  return inner_solve(P, s);
+}
+
+// One defect-correction iteration: rT = r; e = B(rT); x += e; r = b - A x (norm -> scal[0]).
+int iteration_cycles(PlanImpl* P, cudaStream_t s) {
+  int rc;
+  nn4_dtype tt;
+  void* rt;
+  LevelGeom gt;
+  residual_sink(P, &tt, &rt, &gt);
+  if (rt && (rc = K(P, "pointwise:to_inner", s, [&] { return launch_convert(NN4_F64, P->r64, P->g64, tt, rt, gt, s); })))
+    return rc;
+  ZRef z;
+  if ((rc = precondition(P, s, &z))) return rc;
+  if ((rc = K(P, "pointwise:add_correction", s, [&] { return launch_add_correction(z.t, P->x64, P->g64, z.p, z.g, s); })))
     return rc;
   return outer_residual(P, s, P->scal + 0);
 }
 
 // One flexible-CG iteration with parity `par` (p, q buffers and p.q, p.r slots alternate).
 int iteration_fcg(PlanImpl* P, int par, cudaStream_t s) {
-  Level& L0 = P->lv[0];
   const int old = 1 - par;
   int rc;
-  if ((rc = inner_solve(P, s))) return rc;  // z = L0.e from rT = L0.r
+  ZRef z;
+  if ((rc = precondition(P, s, &z))) return rc;
   if ((rc = check_cuda(cudaMemsetAsync(P->scal + 2, 0, sizeof(double), s), "zero zq"))) return rc;
   if ((rc = K(P, "pointwise:dot", s,
-              [&] { return launch_dot_zq(P->T, L0.e, L0.g, P->q64[old], P->g64, P->scal + 2, s); })))
+              [&] { return launch_dot(z.t, z.p, z.g, NN4_F64, P->q64[old], P->g64, P->scal + 2, s); })))
     return rc;
   if ((rc = K(P, "pointwise:direction", s, [&] {
-         return launch_new_direction(P->T, L0.e, L0.g, P->p64[old], P->p64[par], P->g64, P->scal + 2,
-                                     P->scal + 3 + old, s);
+         return launch_direction(z.t, z.p, z.g, NN4_F64, P->p64[old], P->p64[par], P->g64, P->scal + 2,
+                                 P->scal + 3 + old, s);
        })))
     return rc;
   if ((rc = check_cuda(cudaMemsetAsync(P->scal + 3 + par, 0, sizeof(double), s), "zero pq"))) return rc;
@@ -434,17 +557,20 @@ int iteration_fcg(PlanImpl* P, int par, cudaStream_t s) {
   a.norm2 = P->scal + 3 + par;
   a.dot2 = P->scal + 5 + par;
   a.zchunk = P->cfg64.zchunk;
-  a.lk = P->lk64;
+  a.lk = P->vc ? P->lk64 : nullptr;
   if ((rc = K(P, "pass64:matvec", s, [&] {
          return launch_pass(NN4_F64, OP_MATVEC, a, P->p64[par], P->vc ? P->k64 : nullptr, P->cfg64, s,
-                            &P->tm_p64[par], P->vc ? &P->tm_k64 : nullptr);
+                            &P->m_mat64[par]);
        })))
     return rc;
   if ((rc = check_cuda(cudaMemsetAsync(P->scal + 0, 0, sizeof(double), s), "zero norm"))) return rc;
+  nn4_dtype tt;
+  void* rt;
+  LevelGeom gt;
+  residual_sink(P, &tt, &rt, &gt);
   return K(P, "pointwise:fcg_update", s, [&] {
-    return launch_fcg_update(P->T, P->x64, P->r64, P->p64[par], P->q64[par], P->g64,
-                             P->T == NN4_F64 ? nullptr : L0.r, L0.g, P->scal + 5 + par, P->scal + 3 + par,
-                             P->scal + 0, s);
+    return launch_update(NN4_F64, P->x64, P->r64, P->p64[par], P->q64[par], P->g64, tt, rt, gt, P->scal + 5 + par,
+                         P->scal + 3 + par, P->scal + 0, s);
   });
 }
 
@@ -486,14 +612,135 @@ int launch_iteration(PlanImpl* P, int it, cudaStream_t s) {
   return iteration(P, it, s);
 }
 
-int make_level_maps(PlanImpl* P, Level& L) {
-  int bx, by;
-  pass_box(P->T, L.cfg, &bx, &by);
-  if (!make_tmap_3d(&L.tm_t, P->T, L.t, L.g.nx, L.g.ny, L.g.nz, L.g.pitch, bx, by) ||
-      !make_tmap_3d(&L.tm_e, P->T, L.e, L.g.nx, L.g.ny, L.g.nz, L.g.pitch, bx, by))
+int make_level_maps(PlanImpl* P, int l) {
+  Level& L = P->lv[l];
+  if (P->vc && l > 0) return NN4_OK;  // Galerkin levels use the 27-point kernel
+  const void* k = (P->vc && l == 0) ? L.k : nullptr;
+  PassArgs aj = level_args(P, l, L.r, L.e);
+  PassArgs ar = level_args(P, l, L.r, L.t);
+  if (!make_pass_maps(&L.m_jac, P->T, aj, L.cfg, L.t, k) || !make_pass_maps(&L.m_res, P->T, ar, L.cfg, L.e, k))
     return set_error(NN4_ECUDA, "tensor map encode failed");
-  if (L.k && !make_tmap_3d(&L.tm_k, P->T, L.k, L.g.nx, L.g.ny, L.g.nz, L.g.pitch, bx, by))
-    return set_error(NN4_ECUDA, "tensor map encode failed (k)");
+  return NN4_OK;
+}
+
+// Maps of the outer-loop passes (FP64) and of the inner Krylov mat-vec (FP32).
+int make_outer_maps(PlanImpl* P) {
+  PassArgs a{};
+  a.g = P->g64;
+  a.b = P->b64;
+  a.lk = P->vc ? P->lk64 : nullptr;
+  bool ok = make_pass_maps(&P->m_res64, NN4_F64, a, P->cfg64, P->x64, P->vc ? P->k64 : nullptr);
+  if (P->o.outer == NN4_OUTER_FCG) {
+    a.b = P->r64;
+    for (int t = 0; t < 2; ++t)
+      ok = ok && make_pass_maps(&P->m_mat64[t], NN4_F64, a, P->cfg64, P->p64[t], P->vc ? P->k64 : nullptr);
+  }
+  if (P->o.inner_krylov > 0) {
+    PassArgs b{};
+    b.g = P->g32;
+    b.b = P->ri;
+    for (int t = 0; t < 2; ++t)
+      ok = ok && make_pass_maps(&P->m_mat32[t], NN4_F32, b, P->cfg32, P->pi[t], P->vc ? P->k32 : nullptr);
+  }
+  return ok ? NN4_OK : set_error(NN4_ECUDA, "tensor map encode failed");
+}
+
+// ---------------------------------------------------------------- autotuner
+// Picks, for every stencil pass of the plan, the fastest tile shape / pipeline depth / z-march
+// depth among the compiled candidates by timing each on the plan's own arrays (outputs go to
+// buffers that are scratch at plan creation).  Choices are cached per process by
+// (dtype, operator kind, op, grid size).
+struct TuneKey {
+  int dt, vmode, op, nx, ny, nz, iso;
+  bool operator==(const TuneKey& o) const {
+    return dt == o.dt && vmode == o.vmode && op == o.op && nx == o.nx && ny == o.ny && nz == o.nz && iso == o.iso;
+  }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, PassCfg>> g_tune_cache;
+
+int tune_pass(nn4_dtype dt, int op, PassArgs a, const void* x, const void* k, PassCfg* cfg, cudaStream_t s) {
+  const bool iso = a.L.c[1] == 0.0 && a.L.c[2] == 0.0 && a.L.c[4] == 0.0;
+  const TuneKey key{(int)dt, k ? (a.lk ? 2 : 1) : 0, op, a.g.nx, a.g.ny, a.g.nz, iso ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto& e : g_tune_cache)
+      if (e.first == key) {
+        *cfg = e.second;
+        return NN4_OK;
+      }
+  }
+  double* nrm = nullptr;
+  int rc;
+  if ((rc = check_cuda(cudaMalloc(&nrm, 2 * sizeof(double)), "tune scratch"))) return rc;
+  a.norm2 = (op == OP_RESIDUAL || op == OP_MATVEC) ? nrm : nullptr;
+  a.dot2 = op == OP_MATVEC ? nrm + 1 : nullptr;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const PassCfg base = default_pass_cfg(dt, k != nullptr, a.g);
+  float best = 1e30f;
+  PassCfg best_cfg = *cfg;
+  for (int c = 0; c < num_pass_cfgs(); ++c) {
+    for (int zf = 0; zf < 3; ++zf) {
+      const int zc = std::max(4, std::min(a.g.nz, zf == 0 ? base.zchunk : zf == 1 ? base.zchunk * 2 : base.zchunk / 2));
+      PassCfg cand = pass_cfg_candidate(c, a.g, zc);
+      PassMaps m;
+      if (!make_pass_maps(&m, dt, a, cand, x, k)) continue;
+      a.zchunk = cand.zchunk;
+      if (launch_pass(dt, op, a, x, k, cand, s, &m) != NN4_OK) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3; ++r) launch_pass(dt, op, a, x, k, cand, s, &m);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_cfg = cand;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(nrm);
+  if ((rc = check_cuda(cudaGetLastError(), "autotune"))) return rc;
+  *cfg = best_cfg;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.push_back({key, best_cfg});
+  return NN4_OK;
+}
+
+int autotune_plan(PlanImpl* P) {
+  int rc;
+  cudaStream_t s = 0;
+  for (int l = 0; l < (int)P->lv.size(); ++l) {
+    if (P->vc && l > 0) continue;
+    if (P->tail_start > 0 && l >= P->tail_start) continue;
+    Level& L = P->lv[l];
+    PassArgs a = level_args(P, l, L.r, L.e);
+    if ((rc = tune_pass(P->T, OP_JACOBI, a, L.t, (P->vc && l == 0) ? L.k : nullptr, &L.cfg, s))) return rc;
+  }
+  PassArgs a{};
+  a.g = P->g64;
+  a.L = P->L64;
+  a.b = P->b64;
+  a.out = P->r64;
+  a.lk = P->vc ? P->lk64 : nullptr;
+  if ((rc = tune_pass(NN4_F64, P->o.outer == NN4_OUTER_FCG ? OP_MATVEC : OP_RESIDUAL, a, P->x64,
+                      P->vc ? P->k64 : nullptr, &P->cfg64, s)))
+    return rc;
+  if (P->o.inner_krylov > 0) {
+    PassArgs b{};
+    b.g = P->g32;
+    b.L = P->lv[0].L;
+    b.b = P->ri;
+    b.out = P->qi[0];
+    if ((rc = tune_pass(NN4_F32, OP_MATVEC, b, P->pi[1], P->vc ? P->k32 : nullptr, &P->cfg32, s))) return rc;
+  }
   return NN4_OK;
 }
 
@@ -550,9 +797,11 @@ int solve_device(PlanImpl* P, double rtol, int32_t max_iters, nn4_solve_info* in
   if ((rc = outer_residual(P, s, P->scal + 0))) return rc;
   if (P->o.outer == NN4_OUTER_FCG) {
     // r64 holds the residual; rT for the first inner solve; p_old = q_old = 0, p.q_old = 1
-    if (P->T != NN4_F64 && (rc = K(P, "pointwise:to_inner", s, [&] {
-                              return launch_to_inner(P->T, P->r64, P->g64, P->lv[0].r, P->lv[0].g, s);
-                            })))
+    nn4_dtype tt;
+    void* rt;
+    LevelGeom gt;
+    residual_sink(P, &tt, &rt, &gt);
+    if (rt && (rc = K(P, "pointwise:to_inner", s, [&] { return launch_convert(NN4_F64, P->r64, P->g64, tt, rt, gt, s); })))
       return rc;
     const size_t fb = field_bytes(P->g64, NN4_F64);
     for (int t = 0; t < 2; ++t) {
@@ -640,6 +889,9 @@ void nn4_plan_opts_default(nn4_plan_opts* o) {
   o->use_graph = 1;
   o->check_every = 1;
   o->profile = 0;
+  o->inner_krylov = 0;
+  o->coarse_tail = 1;
+  o->autotune = 1;
 }
 
 int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opts, nn4_plan* out) {
@@ -652,6 +904,7 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
   if (opts) o = *opts;
   if (o.inner != NN4_F64 && o.inner != NN4_F32 && o.inner != NN4_BF16) return set_error(NN4_EINVAL, "bad inner dtype");
   if (o.inner_cycles < 1 || o.inner_cycles > 64) return set_error(NN4_EINVAL, "inner_cycles must be in 1..64");
+  if (o.inner_krylov < 0 || o.inner_krylov > 64) return set_error(NN4_EINVAL, "inner_krylov must be in 0..64");
   if (o.outer != NN4_OUTER_CYCLES && o.outer != NN4_OUTER_FCG) return set_error(NN4_EINVAL, "bad outer method");
   if (!(o.omega > 0.0 && o.omega < 2.0)) return set_error(NN4_EINVAL, "omega must lie in (0, 2)");
   if (k && reinterpret_cast<uintptr_t>(k) % 16) return set_error(NN4_EINVAL, "k is not 16-byte aligned");
@@ -687,6 +940,17 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
       P->lv.push_back(c);
     }
   }
+  {
+    const int nl = (int)P->lv.size();
+    for (int l = 1; l < nl; ++l) {
+      const long long nodes = (long long)P->lv[l].g.nx * P->lv[l].g.ny * P->lv[l].g.nz;
+      if (nodes <= kTailNodes && nl - l <= kMaxTail) {
+        P->tail_start = l;
+        break;
+      }
+    }
+    if (!o.coarse_tail) P->tail_start = -1;
+  }
   for (auto& L : P->lv) {
     L.L = stencil_coef(L.h);
     L.cfg = default_pass_cfg(P->T, P->vc && &L == &P->lv[0], L.g);
@@ -704,12 +968,36 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
     return rc;
   }
   if (P->T == NN4_F64) P->lv[0].r = P->r64;
+  {
+    const double one = 1.0;
+    if ((rc = check_cuda(cudaMemcpy(P->scal + 15, &one, sizeof(one), cudaMemcpyHostToDevice), "init scalars"))) {
+      destroy(P);
+      return rc;
+    }
+  }
   if (o.outer == NN4_OUTER_FCG) {
     for (int t = 0; t < 2; ++t)
       if ((rc = alloc(P, (void**)&P->p64[t], fb64)) || (rc = alloc(P, (void**)&P->q64[t], fb64))) {
         destroy(P);
         return rc;
       }
+  }
+  if (o.inner_krylov > 0) {
+    if (P->T == NN4_F64) {
+      destroy(P);
+      return set_error(NN4_EINVAL, "inner_krylov needs an FP32 or BF16 hierarchy");
+    }
+    P->g32 = P->g64;
+    P->g32.pitch = nn4_row_pitch(g->n[0], NN4_F32);
+    P->cfg32 = default_pass_cfg(NN4_F32, P->vc, P->g32);
+    const size_t fb32 = field_bytes(P->g32, NN4_F32);
+    if ((rc = alloc(P, (void**)&P->yi, fb32)) || (rc = alloc(P, (void**)&P->ri, fb32)) ||
+        (rc = alloc(P, (void**)&P->pi[0], fb32)) || (rc = alloc(P, (void**)&P->pi[1], fb32)) ||
+        (rc = alloc(P, (void**)&P->qi[0], fb32)) || (rc = alloc(P, (void**)&P->qi[1], fb32))) {
+      destroy(P);
+      return rc;
+    }
+    if (P->T == NN4_F32) P->lv[0].r = P->ri;  // the V-cycles read the inner residual directly
   }
   if (P->vc) {
     if ((rc = alloc(P, (void**)&P->k64, fb64)) ||
@@ -737,26 +1025,30 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
       destroy(P);
       return rc;
     }
-  }
-  // tensor maps
-  {
-    int bx, by;
-    pass_box(NN4_F64, P->cfg64, &bx, &by);
-    bool ok = make_tmap_3d(&P->tm_x64, NN4_F64, P->x64, g->n[0], g->n[1], g->n[2], g->pitch, bx, by);
-    if (P->vc) ok = ok && make_tmap_3d(&P->tm_k64, NN4_F64, P->k64, g->n[0], g->n[1], g->n[2], g->pitch, bx, by);
-    if (o.outer == NN4_OUTER_FCG)
-      for (int t = 0; t < 2; ++t)
-        ok = ok && make_tmap_3d(&P->tm_p64[t], NN4_F64, P->p64[t], g->n[0], g->n[1], g->n[2], g->pitch, bx, by);
-    if (!ok) {
-      destroy(P);
-      return set_error(NN4_ECUDA, "tensor map encode failed");
-    }
-    for (auto& L : P->lv)
-      if ((rc = make_level_maps(P, L))) {
+    if (o.inner_krylov > 0) {
+      if (P->T == NN4_F32) {
+        P->k32 = static_cast<float*>(P->lv[0].k);
+      } else if ((rc = alloc(P, (void**)&P->k32, field_bytes(P->g32, NN4_F32))) ||
+                 (rc = launch_convert(NN4_F64, P->k64, P->g64, NN4_F32, P->k32, P->g32, 0))) {
         destroy(P);
         return rc;
       }
+    }
   }
+  if (o.autotune && (rc = autotune_plan(P))) {
+    destroy(P);
+    return rc;
+  }
+  // tensor maps of every pass (all pointers and tile shapes are final now)
+  if ((rc = make_outer_maps(P))) {
+    destroy(P);
+    return rc;
+  }
+  for (int l = 0; l < (int)P->lv.size(); ++l)
+    if ((rc = make_level_maps(P, l))) {
+      destroy(P);
+      return rc;
+    }
   // coarse operators and the coarsest inverse
   std::vector<double> dense;
   if (P->vc) {
@@ -796,13 +1088,7 @@ int nn4_vcycle(nn4_plan p, const void* b, void* x, void* stream) {
   if (reinterpret_cast<uintptr_t>(b) % 16 || reinterpret_cast<uintptr_t>(x) % 16)
     return set_error(NN4_EINVAL, "arrays must be 16-byte aligned");
   PlanImpl* P = p->impl;
-  Level& L0 = P->lv[0];
-  int bx, by;
-  pass_box(P->T, L0.cfg, &bx, &by);
-  CUtensorMap tm;
-  if (!make_tmap_3d(&tm, P->T, x, L0.g.nx, L0.g.ny, L0.g.nz, L0.g.pitch, bx, by))
-    return set_error(NN4_ECUDA, "tensor map encode failed");
-  Fine F{b, x, &tm};
+  Fine F{b, x, nullptr, nullptr};  // caller arrays: maps are built per launch
   return vcycle_impl(P, F, false, static_cast<cudaStream_t>(stream));
 }
 

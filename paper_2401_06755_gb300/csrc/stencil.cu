@@ -80,33 +80,48 @@ __device__ __forceinline__ void plane_uv(const T* __restrict__ sx, const T* __re
 }
 
 // VC: 0 constant coefficient; 1 Eq. k-T with L k on the fly; 2 Eq. k-T with L k (and optionally
-// the inverse diagonal) read pointwise.
-template <typename T, int OP, int VC, bool ISO, int RY, int TYT, int S>
-__global__ void __launch_bounds__(32 * TYT)
-    k_pass(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmk,
-           const PassArgs a) {
+// the inverse diagonal) read pointwise.  The CTA covers TX = 32 WX columns and TY = TYT RY rows.
+// Every pipeline stage holds the haloed tiles of input plane p (x, and k for Eq. k-T) and the
+// pointwise tiles (b, L k, 1/diag) of output plane p - 1, all brought by TMA onto one mbarrier,
+// so no global load sits on the critical path of a plane.
+struct Maps {
+  CUtensorMap x, k, b, lk, invd;
+};
+
+template <typename T, int OP, int VC, bool ISO, int WX, int RY, int TYT, int S>
+__global__ void __launch_bounds__(32 * WX * TYT)
+    k_pass(const __grid_constant__ Maps maps, const PassArgs a) {
   using A = typename Acc<T>::type;
   constexpr int AL = kAlign<T>;
-  constexpr int BX = 32 + 2 * AL;
-  constexpr int BY = TYT * RY + 2;
+  constexpr int TX = 32 * WX, TY = TYT * RY;
+  constexpr int BX = TX + 2 * AL;
+  constexpr int BY = TY + 2;
   constexpr int NF = VC ? 2 : 1;
-  constexpr int TILE_BYTES = BX * BY * (int)sizeof(T);
-  constexpr int TILE_PAD = (TILE_BYTES + 127) / 128 * 128;
+  constexpr bool HAS_B = OP != OP_APPLY;
+  constexpr int HALO_BYTES = BX * BY * (int)sizeof(T);
+  constexpr int HALO_PAD = (HALO_BYTES + 127) / 128 * 128;
+  constexpr int PT_BYTES = TX * TY * (int)sizeof(T);
+  constexpr int PT_PAD = (PT_BYTES + 127) / 128 * 128;
+  constexpr int NP = (HAS_B ? 1 : 0) + (VC == 2 ? 2 : 0);  // pointwise slots per stage
+  constexpr int STAGE = NF * HALO_PAD + NP * PT_PAD;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * NF * TILE_PAD);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * STAGE);
   double* red = reinterpret_cast<double*>(bars + S);
 
   const LevelGeom& g = a.g;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * (TYT * RY);
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int zs = blockIdx.z * a.zchunk;
   const int ze = min(nz, zs + a.zchunk);
-  const int tid = threadIdx.x + 32 * threadIdx.y;
+  const int tid = threadIdx.x + TX * threadIdx.y;
   const int nplanes = ze - zs + 2;  // input planes zs-1 .. ze
+  const bool use_invd = VC == 2 && OP == OP_JACOBI && a.invd != nullptr;
+  const int pt_loads = (HAS_B ? 1 : 0) + (VC == 2 ? 1 : 0) + (use_invd ? 1 : 0);
 
   if (tid == 0) {
-    prefetch_tmap(&tmx);
-    if (VC) prefetch_tmap(&tmk);
+    prefetch_tmap(&maps.x);
+    if (VC) prefetch_tmap(&maps.k);
+    if (HAS_B) prefetch_tmap(&maps.b);
 #pragma unroll
     for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
     fence_barrier_init();
@@ -115,10 +130,24 @@ __global__ void __launch_bounds__(32 * TYT)
 
   auto issue = [&](int q) {
     const int s = q % S;
+    unsigned char* st = smem + s * STAGE;
     const int zp = mirror(zs - 1 + q, nz);
-    mbar_expect_tx(&bars[s], NF * TILE_BYTES);
-    tma_load_3d(smem + (s * NF) * TILE_PAD, &tmx, x0 - AL, y0 - 1, zp, &bars[s]);
-    if (VC) tma_load_3d(smem + (s * NF + 1) * TILE_PAD, &tmk, x0 - AL, y0 - 1, zp, &bars[s]);
+    const int kout = zs + q - 2;
+    const bool pt = q >= 2;
+    mbar_expect_tx(&bars[s], NF * HALO_BYTES + (pt ? pt_loads * PT_BYTES : 0));
+    tma_load_3d(st, &maps.x, x0 - AL, y0 - 1, zp, &bars[s]);
+    if (VC) tma_load_3d(st + HALO_PAD, &maps.k, x0 - AL, y0 - 1, zp, &bars[s]);
+    if (pt) {
+      unsigned char* pp = st + NF * HALO_PAD;
+      if (HAS_B) {
+        tma_load_3d(pp, &maps.b, x0, y0, kout, &bars[s]);
+        pp += PT_PAD;
+      }
+      if (VC == 2) {
+        tma_load_3d(pp, &maps.lk, x0, y0, kout, &bars[s]);
+        if (use_invd) tma_load_3d(pp + PT_PAD, &maps.invd, x0, y0, kout, &bars[s]);
+      }
+    }
   };
   if (tid == 0) {
     for (int q = 0; q < min(S, nplanes); ++q) issue(q);
@@ -143,6 +172,9 @@ __global__ void __launch_bounds__(32 * TYT)
 #pragma unroll
   for (int t = 0; t < 8; ++t) c[t] = (A)a.L.c[t];
   const A wx = (A)half_count(ic, nx);
+  A wy[RY];
+#pragma unroll
+  for (int r = 0; r < RY; ++r) wy[r] = wx * (A)half_count(min(jb + r, ny - 1), ny);
 
   Runner<A, RY> sx, skx, sk;  // L~x, L~(kx), L~k
   sx.zero();
@@ -153,12 +185,17 @@ __global__ void __launch_bounds__(32 * TYT)
   A xc1[RY], kc1[RY];  // centre values of the previous input plane (the pending output)
   double nrm = 0.0, dt2 = 0.0;
   bool failed = false;
+  T* out = reinterpret_cast<T*>(a.out);
 
   for (int q = 0; q < nplanes; ++q) {
     const int s = q % S;
     if (!mbar_wait_bounded(&bars[s], (uint32_t)((q / S) & 1))) failed = true;
-    const T* tx_ = reinterpret_cast<const T*>(smem + (s * NF) * TILE_PAD);
-    const T* tk_ = reinterpret_cast<const T*>(smem + (s * NF + 1) * TILE_PAD);
+    const unsigned char* st = smem + s * STAGE;
+    const T* tx_ = reinterpret_cast<const T*>(st);
+    const T* tk_ = reinterpret_cast<const T*>(st + HALO_PAD);
+    const T* tb_ = reinterpret_cast<const T*>(st + NF * HALO_PAD);
+    const T* tl_ = reinterpret_cast<const T*>(st + NF * HALO_PAD + (HAS_B ? PT_PAD : 0));
+    const T* ti_ = tl_ + PT_PAD / sizeof(T);
     A ux[RY], vx[RY], xcn[RY];
     plane_uv<T, A, RY, false, ISO>(tx_, tx_, rowoff, cc, cl, cr, c, ux, vx, xcn);
     A ukx[RY], vkx[RY], uk[RY], vk[RY], kcn[RY];
@@ -168,21 +205,17 @@ __global__ void __launch_bounds__(32 * TYT)
 #pragma unroll
       for (int r = 0; r < RY; ++r) kcn[r] = to_acc(tk_[rowoff[r + 1] + cc]);
     }
-    if (__syncthreads_or(failed)) {
-      failed = true;
-      break;
-    }
-    if (tid == 0 && q + S < nplanes) issue(q + S);
 
     const int kout = zs + q - 2;  // output plane completed by this input plane
+    if (q >= 2 && !failed) {
+      const A wz = (A)half_count(kout, nz);
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-      if (q >= 2) {
+      for (int r = 0; r < RY; ++r) {
         const int j = jb + r;
         if (i < nx && j < ny) {
-          const A w = wx * (A)half_count(j, ny) * (A)half_count(kout, nz);
+          const A w = wy[r] * wz;
           const A Lx = sx.p1[r] + ux[r];
-          const long long idx = (long long)i + g.pitch * ((long long)j + (long long)ny * kout);
+          const int po = (j - y0) * TX + (i - x0);  // pointwise tile offset
           A Ax, D;
           if (VC == 1) {
             const A Lkx = skx.p1[r] + ukx[r];
@@ -191,19 +224,19 @@ __global__ void __launch_bounds__(32 * TYT)
             D = w * (c[0] * kc1[r] - (A)0.5 * Lk);
           } else if (VC == 2) {
             const A Lkx = skx.p1[r] + ukx[r];
-            const A hLk = (A)0.5 * to_acc(reinterpret_cast<const T*>(a.lk)[idx]);  // 1/2 (L k), w included
+            const A hLk = (A)0.5 * to_acc(tl_[po]);  // 1/2 (L k), w included
             Ax = (A)0.5 * w * (Lkx + kc1[r] * Lx) - xc1[r] * hLk;
             D = w * c[0] * kc1[r] - hLk;
           } else {
             Ax = w * Lx;
             D = w * c[0];
           }
-          T* out = reinterpret_cast<T*>(a.out);
+          const long long idx = (long long)i + g.pitch * ((long long)j + (long long)ny * kout);
           if (OP == OP_APPLY) {
             out[idx] = from_acc<T>(Ax);
           } else {
             const bool dirn = on_dirichlet(g, i, j, kout);
-            const A bv = to_acc(reinterpret_cast<const T*>(a.b)[idx]);
+            const A bv = to_acc(tb_[po]);
             if (OP == OP_RESIDUAL) {
               const A rv = dirn ? A(0) : bv - Ax;
               out[idx] = from_acc<T>(rv);
@@ -214,14 +247,16 @@ __global__ void __launch_bounds__(32 * TYT)
               nrm += (double)xc1[r] * (double)qv;
               dt2 += (double)xc1[r] * (double)bv;
             } else {
-              const A corr = (VC == 2 && a.invd) ? (bv - Ax) * to_acc(reinterpret_cast<const T*>(a.invd)[idx])
-                                                  : (bv - Ax) / D;
+              const A corr = use_invd ? (bv - Ax) * to_acc(ti_[po]) : (bv - Ax) / D;
               const A xn = dirn ? xc1[r] : xc1[r] + (A)a.omega * corr;
               out[idx] = from_acc<T>(xn);
             }
           }
         }
       }
+    }
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
       // shift the running sums: the output of this plane still needs u of the next plane
       sx.p1[r] = sx.p2[r] + vx[r];
       sx.p2[r] = ux[r];
@@ -236,6 +271,12 @@ __global__ void __launch_bounds__(32 * TYT)
         sk.p2[r] = uk[r];
       }
     }
+    // every thread is done with stage s: refill it with the plane S ahead
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    if (tid == 0 && q + S < nplanes) issue(q + S);
   }
   if (failed) {
     // drain copies that may still be in flight before the CTA exits
@@ -249,58 +290,64 @@ __global__ void __launch_bounds__(32 * TYT)
   if (OP == OP_MATVEC && a.dot2 != nullptr) block_sum_atomic(dt2, a.dot2, red);
 }
 
-template <typename T, int OP, int VC, bool ISO, int RY, int TYT, int S>
-int launch_t(const PassArgs& a, const CUtensorMap& mx, const CUtensorMap& mk, cudaStream_t st) {
+template <typename T, int OP, int VC, bool ISO, int WX, int RY, int TYT, int S>
+int launch_t(const PassArgs& a, const Maps& maps, cudaStream_t st) {
   constexpr int AL = kAlign<T>;
-  constexpr int BX = 32 + 2 * AL;
-  constexpr int BY = TYT * RY + 2;
+  constexpr int TX = 32 * WX, TY = TYT * RY;
   constexpr int NF = VC ? 2 : 1;
-  constexpr int TILE_PAD = (BX * BY * (int)sizeof(T) + 127) / 128 * 128;
-  const size_t smem = (size_t)S * NF * TILE_PAD + S * 8 + 32 * 8;
-  auto kern = k_pass<T, OP, VC, ISO, RY, TYT, S>;
+  constexpr int HALO_PAD = ((TX + 2 * AL) * (TY + 2) * (int)sizeof(T) + 127) / 128 * 128;
+  constexpr int PT_PAD = (TX * TY * (int)sizeof(T) + 127) / 128 * 128;
+  constexpr int NP = (OP != OP_APPLY ? 1 : 0) + (VC == 2 ? 2 : 0);
+  const size_t smem = (size_t)S * (NF * HALO_PAD + NP * PT_PAD) + S * 8 + 32 * 8;
+  auto kern = k_pass<T, OP, VC, ISO, WX, RY, TYT, S>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(stencil pass)");
   }
-  dim3 grid((a.g.nx + 31) / 32, (a.g.ny + TYT * RY - 1) / (TYT * RY), (a.g.nz + a.zchunk - 1) / a.zchunk);
-  kern<<<grid, dim3(32, TYT), smem, st>>>(mx, mk, a);
+  dim3 grid((a.g.nx + TX - 1) / TX, (a.g.ny + TY - 1) / TY, (a.g.nz + a.zchunk - 1) / a.zchunk);
+  kern<<<grid, dim3(TX, TYT), smem, st>>>(maps, a);
   return check_cuda(cudaGetLastError(), "stencil pass launch");
 }
 
+// The configurations the autotuner chooses from: {WX, RY, TYT, S}.
+constexpr int kCfgs[][4] = {{1, 4, 4, 3}, {2, 2, 4, 4}, {1, 2, 8, 3}, {2, 4, 2, 4}};
+constexpr int kNumCfgs = 4;
+
 template <typename T, int OP, int VC, bool ISO>
-int dispatch_cfg(const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx,
-                 const CUtensorMap& mk, cudaStream_t st) {
-  // The configurations the autotuner chooses from.
-  if (cfg.stages == 3 && cfg.tyt == 4 && cfg.ry == 4) return launch_t<T, OP, VC, ISO, 4, 4, 3>(a, mx, mk, st);
-  if (cfg.stages == 3 && cfg.tyt == 8 && cfg.ry == 2) return launch_t<T, OP, VC, ISO, 2, 8, 3>(a, mx, mk, st);
-  if (cfg.stages == 4 && cfg.tyt == 4 && cfg.ry == 2) return launch_t<T, OP, VC, ISO, 2, 4, 4>(a, mx, mk, st);
+int dispatch_cfg(const PassArgs& a, const PassCfg& cfg, const Maps& m, cudaStream_t st) {
+  for (int c = 0; c < kNumCfgs; ++c)
+    if (cfg.wx == kCfgs[c][0] && cfg.ry == kCfgs[c][1] && cfg.tyt == kCfgs[c][2] && cfg.stages == kCfgs[c][3]) {
+      switch (c) {
+        case 0: return launch_t<T, OP, VC, ISO, 1, 4, 4, 3>(a, m, st);
+        case 1: return launch_t<T, OP, VC, ISO, 2, 2, 4, 4>(a, m, st);
+        case 2: return launch_t<T, OP, VC, ISO, 1, 2, 8, 3>(a, m, st);
+        case 3: return launch_t<T, OP, VC, ISO, 2, 4, 2, 4>(a, m, st);
+      }
+    }
   return set_error(NN4_EINVAL, "unsupported stencil pass configuration");
 }
 
 template <typename T, int OP, int VC>
-int dispatch_iso(bool iso, const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx, const CUtensorMap& mk,
-                 cudaStream_t st) {
-  return iso ? dispatch_cfg<T, OP, VC, true>(a, cfg, mx, mk, st) : dispatch_cfg<T, OP, VC, false>(a, cfg, mx, mk, st);
+int dispatch_iso(bool iso, const PassArgs& a, const PassCfg& cfg, const Maps& m, cudaStream_t st) {
+  return iso ? dispatch_cfg<T, OP, VC, true>(a, cfg, m, st) : dispatch_cfg<T, OP, VC, false>(a, cfg, m, st);
 }
 
 template <typename T, int OP>
-int dispatch_vc(int vc, bool iso, const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx,
-                const CUtensorMap& mk, cudaStream_t st) {
-  if (vc == 0) return dispatch_iso<T, OP, 0>(iso, a, cfg, mx, mk, st);
-  if (vc == 1) return dispatch_iso<T, OP, 1>(iso, a, cfg, mx, mk, st);
-  if constexpr (sizeof(T) == 8) return dispatch_iso<T, OP, 2>(iso, a, cfg, mx, mk, st);
+int dispatch_vc(int vc, bool iso, const PassArgs& a, const PassCfg& cfg, const Maps& m, cudaStream_t st) {
+  if (vc == 0) return dispatch_iso<T, OP, 0>(iso, a, cfg, m, st);
+  if (vc == 1) return dispatch_iso<T, OP, 1>(iso, a, cfg, m, st);
+  if constexpr (sizeof(T) == 8) return dispatch_iso<T, OP, 2>(iso, a, cfg, m, st);
   return set_error(NN4_EINVAL, "precomputed L k is supported for FP64 passes only");
 }
 
 template <typename T>
-int dispatch_op(int op, int vc, const PassArgs& a, const PassCfg& cfg, const CUtensorMap& mx,
-                const CUtensorMap& mk, cudaStream_t st) {
+int dispatch_op(int op, int vc, const PassArgs& a, const PassCfg& cfg, const Maps& m, cudaStream_t st) {
   const bool iso = a.L.c[1] == 0.0 && a.L.c[2] == 0.0 && a.L.c[4] == 0.0;
   switch (op) {
-    case OP_APPLY: return dispatch_vc<T, OP_APPLY>(vc, iso, a, cfg, mx, mk, st);
-    case OP_RESIDUAL: return dispatch_vc<T, OP_RESIDUAL>(vc, iso, a, cfg, mx, mk, st);
-    case OP_JACOBI: return dispatch_vc<T, OP_JACOBI>(vc, iso, a, cfg, mx, mk, st);
-    case OP_MATVEC: return dispatch_vc<T, OP_MATVEC>(vc, iso, a, cfg, mx, mk, st);
+    case OP_APPLY: return dispatch_vc<T, OP_APPLY>(vc, iso, a, cfg, m, st);
+    case OP_RESIDUAL: return dispatch_vc<T, OP_RESIDUAL>(vc, iso, a, cfg, m, st);
+    case OP_JACOBI: return dispatch_vc<T, OP_JACOBI>(vc, iso, a, cfg, m, st);
+    case OP_MATVEC: return dispatch_vc<T, OP_MATVEC>(vc, iso, a, cfg, m, st);
   }
   return set_error(NN4_EINVAL, "bad stencil op");
 }
@@ -309,10 +356,11 @@ int dispatch_op(int op, int vc, const PassArgs& a, const PassCfg& cfg, const CUt
 
 PassCfg default_pass_cfg(nn4_dtype dt, bool vc, const LevelGeom& g) {
   PassCfg c;
+  c.wx = 1;
   c.ry = (dt == NN4_F64 && vc) ? 2 : 4;
   c.tyt = (dt == NN4_F64 && vc) ? 8 : 4;
   c.stages = 3;
-  const int tiles = ((g.nx + 31) / 32) * ((g.ny + c.tyt * c.ry - 1) / (c.tyt * c.ry));
+  const int tiles = ((g.nx + 32 * c.wx - 1) / (32 * c.wx)) * ((g.ny + c.tyt * c.ry - 1) / (c.tyt * c.ry));
   // aim at >= ~1200 CTAs (8 per SM) but keep at least 8 output planes per CTA
   int zc = g.nz;
   while (zc > 8 && tiles * ((g.nz + zc - 1) / zc) < 1216) zc = (zc + 1) / 2;
@@ -320,35 +368,64 @@ PassCfg default_pass_cfg(nn4_dtype dt, bool vc, const LevelGeom& g) {
   return c;
 }
 
+int num_pass_cfgs() { return kNumCfgs; }
+
+PassCfg pass_cfg_candidate(int index, const LevelGeom& g, int zchunk) {
+  PassCfg c;
+  c.wx = kCfgs[index][0];
+  c.ry = kCfgs[index][1];
+  c.tyt = kCfgs[index][2];
+  c.stages = kCfgs[index][3];
+  c.zchunk = zchunk > 0 ? zchunk : g.nz;
+  return c;
+}
+
 int pass_box(nn4_dtype dt, const PassCfg& cfg, int* box_x, int* box_y) {
   const int al = 16 / (int)dtype_size(dt);
-  *box_x = 32 + 2 * al;
+  *box_x = 32 * cfg.wx + 2 * al;
   *box_y = cfg.tyt * cfg.ry + 2;
   return NN4_OK;
 }
 
-int launch_pass(nn4_dtype dt, int op, const PassArgs& a, const void* x, const void* k,
-                const PassCfg& cfg, cudaStream_t s, const CUtensorMap* mx, const CUtensorMap* mk) {
-  CUtensorMap tx, tk;
-  int bx, by;
+int pass_point_box(const PassCfg& cfg, int* box_x, int* box_y) {
+  *box_x = 32 * cfg.wx;
+  *box_y = cfg.tyt * cfg.ry;
+  return NN4_OK;
+}
+
+bool make_pass_maps(PassMaps* m, nn4_dtype dt, const PassArgs& a, const PassCfg& cfg, const void* x, const void* k) {
+  int bx, by, px, py;
   pass_box(dt, cfg, &bx, &by);
-  if (!mx) {
-    if (!make_tmap_3d(&tx, dt, x, a.g.nx, a.g.ny, a.g.nz, a.g.pitch, bx, by))
-      return set_error(NN4_ECUDA, "cuTensorMapEncodeTiled failed for x");
-    mx = &tx;
+  pass_point_box(cfg, &px, &py);
+  const LevelGeom& g = a.g;
+  bool ok = make_tmap_3d(&m->x, dt, x, g.nx, g.ny, g.nz, g.pitch, bx, by);
+  if (k) ok = ok && make_tmap_3d(&m->k, dt, k, g.nx, g.ny, g.nz, g.pitch, bx, by);
+  if (a.b) ok = ok && make_tmap_3d(&m->b, dt, a.b, g.nx, g.ny, g.nz, g.pitch, px, py);
+  if (a.lk) ok = ok && make_tmap_3d(&m->lk, dt, a.lk, g.nx, g.ny, g.nz, g.pitch, px, py);
+  if (a.invd) ok = ok && make_tmap_3d(&m->invd, dt, a.invd, g.nx, g.ny, g.nz, g.pitch, px, py);
+  return ok;
+}
+
+int launch_pass(nn4_dtype dt, int op, const PassArgs& a, const void* x, const void* k,
+                const PassCfg& cfg, cudaStream_t s, const PassMaps* pm) {
+  PassMaps local;
+  const bool vc = k != nullptr;
+  if (!pm) {
+    if (!make_pass_maps(&local, dt, a, cfg, x, k)) return set_error(NN4_ECUDA, "cuTensorMapEncodeTiled failed");
+    pm = &local;
   }
-  const bool vc = (k != nullptr) || (mk != nullptr);
-  if (vc && !mk) {
-    if (!make_tmap_3d(&tk, dt, k, a.g.nx, a.g.ny, a.g.nz, a.g.pitch, bx, by))
-      return set_error(NN4_ECUDA, "cuTensorMapEncodeTiled failed for k");
-    mk = &tk;
-  }
-  if (!vc) mk = mx;
+  Maps m;
+  m.x = pm->x;
+  m.k = vc ? pm->k : pm->x;
+  m.b = a.b ? pm->b : pm->x;
+  m.lk = a.lk ? pm->lk : pm->x;
+  m.invd = a.invd ? pm->invd : pm->x;
+  if (op != OP_APPLY && !a.b) return set_error(NN4_EINVAL, "stencil pass needs b");
   const int vmode = vc ? (a.lk ? 2 : 1) : 0;
   switch (dt) {
-    case NN4_F64: return dispatch_op<double>(op, vmode, a, cfg, *mx, *mk, s);
-    case NN4_F32: return dispatch_op<float>(op, vmode, a, cfg, *mx, *mk, s);
-    case NN4_BF16: return dispatch_op<bf16>(op, vmode, a, cfg, *mx, *mk, s);
+    case NN4_F64: return dispatch_op<double>(op, vmode, a, cfg, m, s);
+    case NN4_F32: return dispatch_op<float>(op, vmode, a, cfg, m, s);
+    case NN4_BF16: return dispatch_op<bf16>(op, vmode, a, cfg, m, s);
   }
   return set_error(NN4_EINVAL, "bad dtype");
 }

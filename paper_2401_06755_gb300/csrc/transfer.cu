@@ -47,45 +47,55 @@ __global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ rc, const L
 
 // One thread per fine node: e_f(i) (+)= sum over the coarse nodes bracketing i of
 // prod_d (1 at an even index, 1/2 for each of the two parents at an odd index) e_c.
+// One thread per fine (i, j) column and a run of kPz fine planes: e_f (+)= sum over the coarse
+// nodes bracketing each fine node of prod_d (1 at an even index, 1/2 for each of the two parents
+// at an odd index) e_c.
+constexpr int kPz = 8;
+
 template <typename T>
 __global__ void k_prolong(const T* __restrict__ ec, T* ef, const T* base, const LevelGeom gc,
                           const LevelGeom gf) {
   using A = typename Acc<T>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
   if (i >= gf.nx || j >= gf.ny) return;
-  const long long idx = i + gf.pitch * ((long long)j + (long long)gf.ny * k);
-  if (dir_node(gf, i, j, k)) {
-    ef[idx] = base ? base[idx] : from_acc<T>(A(0));
-    return;
-  }
-  const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-  const int I1 = I0 + (i & 1), J1 = J0 + (j & 1), K1 = K0 + (k & 1);
-  const A wx = (i & 1) ? A(0.5) : A(1), wy = (j & 1) ? A(0.5) : A(1), wz = (k & 1) ? A(0.5) : A(1);
-  auto at = [&](int I, int J, int K) {
-    return to_acc(ec[I + gc.pitch * ((long long)J + (long long)gc.ny * K)]);
-  };
-  A v = at(I0, J0, K0);
-  if (i & 1) v += at(I1, J0, K0);
-  if (j & 1) {
-    A t = at(I0, J1, K0);
-    if (i & 1) t += at(I1, J1, K0);
-    v += t;
-  }
-  if (k & 1) {
-    A t = at(I0, J0, K1);
-    if (i & 1) t += at(I1, J0, K1);
+  const int I0 = i >> 1, J0 = j >> 1;
+  const int I1 = I0 + (i & 1), J1 = J0 + (j & 1);
+  const A wxy = ((i & 1) ? A(0.5) : A(1)) * ((j & 1) ? A(0.5) : A(1));
+  const bool dxy = (gf.dir[0] && i == 0) || (gf.dir[1] && i == gf.nx - 1) || (gf.dir[2] && j == 0) ||
+                   (gf.dir[3] && j == gf.ny - 1);
+  // in-plane interpolation of coarse plane K at (i, j)
+  auto plane = [&](int K) {
+    const T* p = ec + gc.pitch * (long long)gc.ny * K;
+    A v = to_acc(p[I0 + gc.pitch * (long long)J0]);
+    if (i & 1) v += to_acc(p[I1 + gc.pitch * (long long)J0]);
     if (j & 1) {
-      A t2 = at(I0, J1, K1);
-      if (i & 1) t2 += at(I1, J1, K1);
-      t += t2;
+      A t = to_acc(p[I0 + gc.pitch * (long long)J1]);
+      if (i & 1) t += to_acc(p[I1 + gc.pitch * (long long)J1]);
+      v += t;
     }
-    v += t;
+    return v * wxy;
+  };
+  const int k0 = blockIdx.z * kPz, k1 = min(gf.nz, k0 + kPz);
+  A lo = plane(k0 >> 1);
+  for (int k = k0; k < k1; ++k) {
+    const long long idx = i + gf.pitch * ((long long)j + (long long)gf.ny * k);
+    A v;
+    if (k & 1) {
+      const A hi = plane((k >> 1) + 1);
+      v = A(0.5) * (lo + hi);
+      lo = hi;  // the next (even) fine plane injects coarse plane (k >> 1) + 1
+    } else {
+      v = lo;  // coarse plane k / 2 (set before the loop or by the previous odd plane)
+    }
+    const bool dn = dxy || (gf.dir[4] && k == 0) || (gf.dir[5] && k == gf.nz - 1);
+    if (dn) {
+      ef[idx] = base ? base[idx] : from_acc<T>(A(0));
+      continue;
+    }
+    if (base) v += to_acc(base[idx]);
+    ef[idx] = from_acc<T>(v);
   }
-  v *= wx * wy * wz;
-  if (base) v += to_acc(base[idx]);
-  ef[idx] = from_acc<T>(v);
 }
 
 template <typename T>
@@ -100,7 +110,7 @@ template <typename T>
 int prolong_t(const void* ec, const LevelGeom& gc, void* ef, const void* base, const LevelGeom& gf,
               cudaStream_t s) {
   dim3 blk(32, 4);
-  dim3 grd((gf.nx + 31) / 32, (gf.ny + 3) / 4, gf.nz);
+  dim3 grd((gf.nx + 31) / 32, (gf.ny + 3) / 4, (gf.nz + kPz - 1) / kPz);
   k_prolong<T><<<grd, blk, 0, s>>>(static_cast<const T*>(ec), static_cast<T*>(ef), static_cast<const T*>(base), gc, gf);
   return check_cuda(cudaGetLastError(), "prolong launch");
 }

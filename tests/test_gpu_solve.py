@@ -70,14 +70,17 @@ def test_vcycle_fp64_per_cycle(ci):
     k = _sphere_k(g) if vc else None
     b = _rhs(g, 1 + ci)
     lv = mg.Levels(g, k)
-    plan = nn4.Plan(G, nn4.to_field(k, G) if vc else None)
-    B, X = nn4.to_field(b, G), nn4.field(G)
+    K = nn4.to_field(k, G) if vc else None
+    plans = [nn4.Plan(G, K), nn4.Plan(G, K, coarse_tail=False)]
+    B = nn4.to_field(b, G)
+    Xs = [nn4.field(G), nn4.field(G)]
     x = np.zeros(g.shape)
     for c in range(6):
         x = mg.vcycle(lv, x, b)
-        plan.vcycle(B, X)
-        xg = nn4.nodes(X, G).cpu().numpy()
-        assert _rel(xg, x) <= 1e-12, f"cycle {c}: {_rel(xg, x):.3e}"
+        for plan, X in zip(plans, Xs):
+            plan.vcycle(B, X)
+            xg = nn4.nodes(X, G).cpu().numpy()
+            assert _rel(xg, x) <= 1e-12, f"cycle {c}: {_rel(xg, x):.3e}"
 
 
 def test_solve_fp64_fixed_cycles_history():
@@ -184,3 +187,32 @@ def test_error_paths():
     info = plan.solve(nn4.to_field(b, G), nn4.field(G), rtol=1e-14, max_iters=3)
     assert info["status"] == nn4.ENOCONV and info["iterations"] == 3
     assert nn4.device_error() == nn4.OK
+
+
+@pytest.mark.parametrize("inner", ["f32", "bf16"])
+def test_inner_krylov_sphere_error(inner):
+    """Precision form with the FP32 inner flexible-CG loop: few FP64 outer iterations, the
+    solution agrees with the FP64 oracle's to <= 1e-8 (means removed)."""
+    need_gpu()
+    nn4 = _nn4()
+    g, G = _grids((65,) * 3, (1 / 64,) * 3, (False,) * 6)
+    k = _sphere_k(g)
+    b = _rhs(g, 1)
+    xref, _ = mg.pressure_solve_fcg(g, b, k=k, rtol=1e-13, max_iters=200)
+    plan = nn4.Plan(G, nn4.to_field(k, G), inner=nn4.F32 if inner == "f32" else nn4.BF16,
+                    inner_cycles=1, outer=nn4.OUTER_FCG, inner_krylov=12)
+    B, X = nn4.to_field(b, G), nn4.field(G)
+    info = plan.solve(B, X, rtol=1e-10, max_iters=50)
+    assert info["status"] == nn4.OK and info["iterations"] <= 10
+    xg = nn4.nodes(X, G).cpu().numpy()
+    m = fem.lumped_mass(g.shape, g.h)
+    mean = lambda v: (m * v).sum() / m.sum()
+    assert _rel(xg - mean(xg), xref - mean(xref)) <= 1e-8
+    # defect-correction outer loop with the same inner loop
+    plan2 = nn4.Plan(G, nn4.to_field(k, G), inner=nn4.F32, inner_cycles=1, outer=nn4.OUTER_CYCLES,
+                     inner_krylov=12)
+    X2 = nn4.field(G)
+    info2 = plan2.solve(B, X2, rtol=1e-10, max_iters=50)
+    assert info2["status"] == nn4.OK
+    xg2 = nn4.nodes(X2, G).cpu().numpy()
+    assert _rel(xg2 - mean(xg2), xref - mean(xref)) <= 1e-8
