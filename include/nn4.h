@@ -198,6 +198,46 @@ typedef struct {
 
 int nn4_plan_query(nn4_plan p, nn4_plan_info* out);
 
+/* ----------------------------------------------------------------- explicit multiphase terms */
+
+/* Constants of the compressive Petrov-Galerkin volume-fraction scheme (Sections 2.3.5-2.3.6). */
+typedef struct {
+  double dt;         /* time step */
+  double alpha_a;    /* Eq. a_psi: 2 */
+  double eps_k;      /* Eq. k-abs: 1e-7 */
+  double K_plus;     /* weight w+: 300 */
+  double K_minus;    /* weight w-: 300 */
+  double beta;       /* Eq. negativek: 0.1 */
+  double eps_x;      /* Eqs. negativek, normalisation: 1e-4 */
+  double K_pos;      /* Eq. positivek: 3 */
+  double alpha_min;  /* Eq. alpha_min_and_max: 1e-4 */
+  double alpha_max;  /* Eq. alpha_min_and_max: 0.05 */
+  double detect_hi;  /* detector override C > 0.95 */
+  double detect_lo;  /* detector override C < 0.05 */
+  int32_t p;         /* polynomial order (1: linear filters) */
+} nn4_vof_params;
+
+/* Fills p with the paper's constants and the given time step. */
+void nn4_vof_params_default(nn4_vof_params* p, double dt);
+
+/* Bytes of device workspace nn4_vof_advect_residual needs for grid g (7 FP64 fields), or -1. */
+int64_t nn4_vof_workspace_bytes(const nn4_grid* g);
+
+/* One explicit volume-fraction step (Stage 4 of Section 2.4): s_C of Eq. Petrov-Cs (advection
+ * with the first-derivative filters plus the compressive directional Petrov-Galerkin diffusion
+ * of Section 2.3.6 in the form of Eq. k-Txx) and, if C_next != NULL, C_next = C - dt m^-1 s_C
+ * (Eq. transport-indicator-1, m the lumped nodal volume).  C, u, v, w (q^{n+1}), s_C, C_next:
+ * FP64 device arrays on g; workspace: nn4_vof_workspace_bytes(g) bytes of device memory owned by
+ * the caller (contents overwritten).  Natural faces for C; the oscillation detector uses the
+ * copy-halo of Section 2.3.3 at walls.  All arithmetic FP64. */
+int nn4_vof_advect_residual(const nn4_grid* g, const nn4_vof_params* p, const double* C, const double* u,
+                            const double* v, const double* w, double* s_C, double* C_next, void* workspace,
+                            void* stream);
+
+/* *out (device FP64) = sum_i m_i C_i with m the lumped nodal volume: the C(t) of the mass
+ * diagnostic (Section 3, mass conservation), accumulated in FP64. */
+int nn4_mass_sum(const nn4_grid* g, const double* C, double* out, void* stream);
+
 /* ----------------------------------------------------------------- diagnostics */
 
 const char* nn4_last_error(void);

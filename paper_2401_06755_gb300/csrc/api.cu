@@ -139,7 +139,7 @@ const char* nn4_version(void) { return "nn4-gb300 0.1 (sm_103a)"; }
 int nn4_device_error(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return check_cuda(e, "device synchronise");
-  const unsigned int w = stencil_error_word();
+  const unsigned int w = stencil_error_word() | flow_error_word();
   if (w & 1u) return set_error(NN4_ETIMEOUT, "a bounded device wait gave up");
   if (w & 2u) return set_error(NN4_EBOUNDS, "a checked device index was out of range");
   return NN4_OK;

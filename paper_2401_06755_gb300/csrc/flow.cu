@@ -1,0 +1,293 @@
+// Explicit multiphase terms in FP64: the compressive Petrov-Galerkin volume-fraction update of
+// Section 2.3 (Eqs. Petrov-C, Petrov-Cs, a_psi, efficient-kabs, Sx-lin, negativek,
+// normalisation, positivek, alpha_min_and_max, transport-indicator-1) and the lumped-mass total
+// of the mass diagnostic.  These kernels are FP64-ALU bound (several hundred flops per node on a
+// part with 1.2 FP64 TFLOP/s), so they are plain one-thread-per-node kernels that read
+// neighbours through L1; every Q1 filter is applied sum-factorised with boundary-aware 1D
+// element factors (natural truncation).
+#include "common.cuh"
+#include "internal.h"
+
+namespace nn4 {
+
+NN4_DEFINE_ERROR_ACCESSOR(flow_error_word)
+
+namespace {
+
+struct FlowGeom {
+  int nx, ny, nz;
+  long long pitch;
+  double h[3];
+};
+
+__device__ __forceinline__ long long fo(const FlowGeom& g, int i, int j, int k) {
+  return i + g.pitch * ((long long)j + (long long)g.ny * k);
+}
+
+// 1D assembled Q1 factors at node i (n nodes, spacing h) for offset d in {-1, 0, 1}:
+// K stiffness, M mass, G first derivative (int N_i dN_j/dx), L lumped (diagonal of M's rows).
+struct F1 {
+  double K[3], M[3], G[3];
+};
+
+__device__ __forceinline__ F1 factors(int i, int n, double h) {
+  const double eL = i > 0 ? 1.0 : 0.0, eR = i < n - 1 ? 1.0 : 0.0;
+  F1 f;
+  f.K[0] = -eL / h;
+  f.K[1] = (eL + eR) / h;
+  f.K[2] = -eR / h;
+  f.M[0] = eL * h / 6.0;
+  f.M[1] = (eL + eR) * h / 3.0;
+  f.M[2] = eR * h / 6.0;
+  f.G[0] = -0.5 * eL;
+  f.G[1] = 0.5 * (eL - eR);
+  f.G[2] = 0.5 * eR;
+  return f;
+}
+
+__device__ __forceinline__ double lumped(int i, int n, double h) {
+  return 0.5 * h * ((i > 0) + (i < n - 1));
+}
+
+// sum_{dx,dy,dz} ax[dx] ay[dy] az[dz] f(i+dx, j+dy, k+dz) over existing neighbours (the factors
+// of missing neighbours are zero; their index is clamped to stay in bounds).
+__device__ __forceinline__ double tp(const FlowGeom& g, const double* __restrict__ f, int i, int j, int k,
+                                     const double* ax, const double* ay, const double* az) {
+  double sz = 0.0;
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int kk = min(max(k + dz, 0), g.nz - 1);
+    double sy = 0.0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int jj = min(max(j + dy, 0), g.ny - 1);
+      const double* row = f + g.pitch * ((long long)jj + (long long)g.ny * kk);
+      const double sx = ax[0] * row[max(i - 1, 0)] + ax[1] * row[i] + ax[2] * row[min(i + 1, g.nx - 1)];
+      sy += ay[dy + 1] * sx;
+    }
+    sz += az[dz + 1] * sy;
+  }
+  return sz;
+}
+
+// Same with the product field a*b formed on the fly.
+__device__ __forceinline__ double tp2(const FlowGeom& g, const double* __restrict__ a, const double* __restrict__ b,
+                                      int i, int j, int k, const double* ax, const double* ay, const double* az) {
+  double sz = 0.0;
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int kk = min(max(k + dz, 0), g.nz - 1);
+    double sy = 0.0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int jj = min(max(j + dy, 0), g.ny - 1);
+      const long long r = g.pitch * ((long long)jj + (long long)g.ny * kk);
+      const int il = max(i - 1, 0), ir = min(i + 1, g.nx - 1);
+      const double sx = ax[0] * a[r + il] * b[r + il] + ax[1] * a[r + i] * b[r + i] + ax[2] * a[r + ir] * b[r + ir];
+      sy += ay[dy + 1] * sx;
+    }
+    sz += az[dz + 1] * sy;
+  }
+  return sz;
+}
+
+#define NN4_NODE(G)                                        \
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;     \
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;     \
+  const int k = blockIdx.z;                                \
+  if (i >= (G).nx || j >= (G).ny) return;                  \
+  const long long o = fo(G, i, j, k);
+
+// Step 1: raw first-derivative filters f(C; w_d) and the advective derivative u . grad C with
+// the pointwise gradient m^-1 f(C; w_d).
+__global__ void k_vof_grad(const FlowGeom g, const double* __restrict__ C, const double* __restrict__ u,
+                           const double* __restrict__ v, const double* __restrict__ w, double* __restrict__ fx,
+                           double* __restrict__ fy, double* __restrict__ fz, double* __restrict__ gadv) {
+  NN4_NODE(g)
+  const F1 X = factors(i, g.nx, g.h[0]), Y = factors(j, g.ny, g.h[1]), Z = factors(k, g.nz, g.h[2]);
+  const double m = lumped(i, g.nx, g.h[0]) * lumped(j, g.ny, g.h[1]) * lumped(k, g.nz, g.h[2]);
+  const double gx = tp(g, C, i, j, k, X.G, Y.M, Z.M);
+  const double gy = tp(g, C, i, j, k, X.M, Y.G, Z.M);
+  const double gz = tp(g, C, i, j, k, X.M, Y.M, Z.G);
+  fx[o] = gx;
+  fy[o] = gy;
+  fz[o] = gz;
+  gadv[o] = (u[o] * gx + v[o] * gy + w[o] * gz) / m;
+}
+
+__device__ __forceinline__ double detector(const double* __restrict__ C, long long o, long long stride, int idx,
+                                           int n) {
+  const double c0 = C[o];
+  const double cm = idx > 0 ? C[o - stride] : c0;  // copy-halo at walls
+  const double cp = idx < n - 1 ? C[o + stride] : c0;
+  return (c0 - cm) * (cp - c0);
+}
+
+// Step 2: the directional diffusion coefficients k^x, k^y, k^z.
+__global__ void k_vof_coef(const FlowGeom g, const nn4_vof_params p, const double* __restrict__ C,
+                           const double* __restrict__ fx, const double* __restrict__ fy,
+                           const double* __restrict__ fz, const double* __restrict__ gadv,
+                           const double* __restrict__ u, const double* __restrict__ v,
+                           const double* __restrict__ w, double* __restrict__ kx, double* __restrict__ ky,
+                           double* __restrict__ kz) {
+  NN4_NODE(g)
+  const F1 X = factors(i, g.nx, g.h[0]), Y = factors(j, g.ny, g.h[1]), Z = factors(k, g.nz, g.h[2]);
+  const double m = lumped(i, g.nx, g.h[0]) * lumped(j, g.ny, g.h[1]) * lumped(k, g.nz, g.h[2]);
+  const double cx = fx[o] / m, cy = fy[o] / m, cz = fz[o] / m;
+  // Eq. a_psi: alpha_a f(u . grad C; w_m / m - E)
+  const double a_C = p.alpha_a * (tp(g, gadv, i, j, k, X.M, Y.M, Z.M) / m - gadv[o]);
+  // Eq. efficient-kabs (general spacing)
+  const double ax = fabs(cx), ay = fabs(cy), az = fabs(cz);
+  const double sabs = ax + ay + az;
+  const double alpha_kabs = 1.0 / (8.0 * (double)(1 << p.p));
+  const double k_abs = alpha_kabs * fabs(a_C) * (g.h[0] * ax + g.h[1] * ay + g.h[2] * az) /
+                       (p.eps_k + sabs * sabs / 3.0);
+  // Eqs. negativek and normalisation
+  const double gradsq = cx * cx + cy * cy + cz * cz;
+  const double uu = u[o], vv = v[o], ww = w[o];
+  const double proj = (uu * cx + vv * cy + ww * cz) / (p.eps_x + gradsq);
+  const double us = fabs(cx * proj) + fabs(cy * proj) + fabs(cz * proj);
+  const double k_neg = -p.beta * (uu * uu + vv * vv + ww * ww) / (p.eps_x + gradsq * us / 3.0);
+  // detectors with the override, weights, positive / negative parts, clamp (Eq. alpha_min_and_max)
+  const double c0 = C[o];
+  const bool over = c0 > p.detect_hi || c0 < p.detect_lo;
+  const double hmax = fmax(g.h[0], fmax(g.h[1], g.h[2])), hmin = fmin(g.h[0], fmin(g.h[1], g.h[2]));
+  const double kmin = p.alpha_min * hmax * hmax / p.dt, kmax = p.alpha_max * hmin * hmin / p.dt;
+  const long long sy = g.pitch, sz = g.pitch * (long long)g.ny;
+  const double S[3] = {over ? -1.0 : detector(C, o, 1, i, g.nx), over ? -1.0 : detector(C, o, sy, j, g.ny),
+                       over ? -1.0 : detector(C, o, sz, k, g.nz)};
+  double kd[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double wp = -fmax(-1.0, fmin(0.0, p.K_plus * S[d]));
+    const double wm = fmin(1.0, fmax(0.0, p.K_minus * S[d]));
+    const double kk = wp * (p.K_pos * k_abs) + wm * (k_neg / g.h[d]);
+    kd[d] = fmax(-kmin, fmin(kmax, kk));
+  }
+  kx[o] = kd[0];
+  ky[o] = kd[1];
+  kz[o] = kd[2];
+}
+
+// Step 3: s_C of Eq. Petrov-Cs and the update of Eq. transport-indicator-1.
+__global__ void k_vof_update(const FlowGeom g, const nn4_vof_params p, const double* __restrict__ C,
+                             const double* __restrict__ fx, const double* __restrict__ fy,
+                             const double* __restrict__ fz, const double* __restrict__ kx,
+                             const double* __restrict__ ky, const double* __restrict__ kz,
+                             const double* __restrict__ u, const double* __restrict__ v,
+                             const double* __restrict__ w, double* __restrict__ sC, double* __restrict__ Cn) {
+  NN4_NODE(g)
+  const F1 X = factors(i, g.nx, g.h[0]), Y = factors(j, g.ny, g.h[1]), Z = factors(k, g.nz, g.h[2]);
+  const double m = lumped(i, g.nx, g.h[0]) * lumped(j, g.ny, g.h[1]) * lumped(k, g.nz, g.h[2]);
+  double s = u[o] * fx[o] + v[o] * fy[o] + w[o] * fz[o];
+  const double c0 = C[o];
+  const double* kf[3] = {kx, ky, kz};
+  // directional second-derivative filters w_dd^PG = K(d) x M x M, each in Eq. k-Txx form
+  const double* ax[3] = {X.K, X.M, X.M};
+  const double* ay[3] = {Y.M, Y.K, Y.M};
+  const double* az[3] = {Z.M, Z.M, Z.K};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double kc = kf[d][o];
+    const double DkC = tp2(g, kf[d], C, i, j, k, ax[d], ay[d], az[d]);
+    const double DC = tp(g, C, i, j, k, ax[d], ay[d], az[d]);
+    const double Dk = tp(g, kf[d], i, j, k, ax[d], ay[d], az[d]);
+    s += 0.5 * (DkC + kc * DC - c0 * Dk);
+  }
+  sC[o] = s;
+  if (Cn) Cn[o] = c0 - p.dt * s / m;
+}
+
+// Lumped-mass total: sum_i m_i C_i in FP64 (one atomic per block).
+__global__ void k_mass(const FlowGeom g, const double* __restrict__ C, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i < g.nx && j < g.ny)
+    s = lumped(i, g.nx, g.h[0]) * lumped(j, g.ny, g.h[1]) * lumped(k, g.nz, g.h[2]) * C[fo(g, i, j, k)];
+  block_sum_atomic(s, out, red);
+}
+
+FlowGeom flow_geom(const nn4_grid* g) {
+  FlowGeom f;
+  f.nx = g->n[0];
+  f.ny = g->n[1];
+  f.nz = g->n[2];
+  f.pitch = g->pitch;
+  for (int d = 0; d < 3; ++d) f.h[d] = g->h[d];
+  return f;
+}
+
+}  // namespace
+
+int validate_grid(const nn4_grid* g, nn4_dtype dt, int min_n);
+int validate_ptr(const void* p, const char* name);
+
+}  // namespace nn4
+
+using namespace nn4;
+
+extern "C" {
+
+void nn4_vof_params_default(nn4_vof_params* p, double dt) {
+  if (!p) return;
+  p->dt = dt;
+  p->alpha_a = 2.0;
+  p->eps_k = 1e-7;
+  p->K_plus = 300.0;
+  p->K_minus = 300.0;
+  p->beta = 0.1;
+  p->eps_x = 1e-4;
+  p->K_pos = 3.0;
+  p->alpha_min = 1e-4;
+  p->alpha_max = 0.05;
+  p->detect_hi = 0.95;
+  p->detect_lo = 0.05;
+  p->p = 1;
+}
+
+int64_t nn4_vof_workspace_bytes(const nn4_grid* g) {
+  if (!g || g->pitch <= 0) return -1;
+  return 7LL * g->pitch * g->n[1] * g->n[2] * (int64_t)sizeof(double);
+}
+
+int nn4_vof_advect_residual(const nn4_grid* g, const nn4_vof_params* p, const double* C, const double* u,
+                            const double* v, const double* w, double* s_C, double* C_next, void* workspace,
+                            void* stream) {
+  int rc;
+  if ((rc = validate_grid(g, NN4_F64, 2)) || (rc = validate_ptr(C, "C")) || (rc = validate_ptr(u, "u")) ||
+      (rc = validate_ptr(v, "v")) || (rc = validate_ptr(w, "w")) || (rc = validate_ptr(s_C, "s_C")) ||
+      (rc = validate_ptr(workspace, "workspace")))
+    return rc;
+  if (!p) return set_error(NN4_EINVAL, "params is NULL");
+  if (!(p->dt > 0.0) || p->p < 1 || p->p > 3) return set_error(NN4_EINVAL, "bad VOF parameters");
+  if (C_next && (rc = validate_ptr(C_next, "C_next"))) return rc;
+  if (s_C == C || C_next == C) return set_error(NN4_EINVAL, "outputs must not alias C");
+  const FlowGeom fg = flow_geom(g);
+  const size_t f = (size_t)g->pitch * g->n[1] * g->n[2];
+  double* ws = static_cast<double*>(workspace);
+  double *fx = ws, *fy = ws + f, *fz = ws + 2 * f, *ga = ws + 3 * f, *kx = ws + 4 * f, *ky = ws + 5 * f,
+         *kz = ws + 6 * f;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  dim3 blk(32, 4), grd((fg.nx + 31) / 32, (fg.ny + 3) / 4, fg.nz);
+  k_vof_grad<<<grd, blk, 0, s>>>(fg, C, u, v, w, fx, fy, fz, ga);
+  k_vof_coef<<<grd, blk, 0, s>>>(fg, *p, C, fx, fy, fz, ga, u, v, w, kx, ky, kz);
+  k_vof_update<<<grd, blk, 0, s>>>(fg, *p, C, fx, fy, fz, kx, ky, kz, u, v, w, s_C, C_next);
+  return check_cuda(cudaGetLastError(), "VOF kernels");
+}
+
+int nn4_mass_sum(const nn4_grid* g, const double* C, double* out, void* stream) {
+  int rc;
+  if ((rc = validate_grid(g, NN4_F64, 2)) || (rc = validate_ptr(C, "C"))) return rc;
+  if (!out) return set_error(NN4_EINVAL, "out is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((rc = check_cuda(cudaMemsetAsync(out, 0, sizeof(double), s), "zero mass"))) return rc;
+  const FlowGeom fg = flow_geom(g);
+  dim3 blk(32, 4), grd((fg.nx + 31) / 32, (fg.ny + 3) / 4, fg.nz);
+  k_mass<<<grd, blk, 0, s>>>(fg, C, out);
+  return check_cuda(cudaGetLastError(), "mass sum");
+}
+
+}  // extern "C"

@@ -64,6 +64,7 @@ size_t dtype_size(nn4_dtype dt);
 
 // Per-unit device error words (read and cleared).
 unsigned int stencil_error_word();
+unsigned int flow_error_word();
 
 // ---------------------------------------------------------------- launchers
 // Tensor maps of one stencil pass: haloed tiles of x and k, pointwise tiles of b, L k, 1/diag.
@@ -101,7 +102,7 @@ int launch_coarse_solve(nn4_dtype dt, const double* ainv, const int* free_idx, i
 // entry level (its r holds the restricted residual on entry, its e the correction on exit);
 // the last level is the coarsest (dense solve with ainv over free_idx).
 constexpr int kMaxTail = 8;
-constexpr int kTailNodes = 6000;  // levels at or below this many nodes join the tail
+constexpr int kTailNodes = 800;  // levels at or below this many nodes join the tail (9^3)
 
 struct TailLevel {
   LevelGeom g;

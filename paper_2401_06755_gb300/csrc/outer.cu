@@ -1,6 +1,8 @@
 // Pointwise FP64 kernels of the outer loop of the pressure solve: defect-correction update,
 // conversion of the FP64 residual to the inner storage type, and the flexible-CG recurrences
 // (Notay 2000) with their dot products.  All sums are accumulated in FP64.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 #include "outer.h"
@@ -44,14 +46,17 @@ __global__ void k_norm_masked(const double* __restrict__ v, LevelGeom g, double*
   block_sum_atomic(s, out, red);
 }
 
-// out += sum z_i * q_i (z of type TZ, q of type V)
+// out += sum z_i * q_i (z of type TZ, q of type V).  With a low-precision z the products and the
+// per-thread partial sums are FP32 (they only set the conjugation coefficient of flexible CG);
+// the sum across threads is FP64.
 template <typename TZ, typename V>
 __global__ void k_dot_zq(const TZ* __restrict__ z, LevelGeom gz, const V* __restrict__ q, LevelGeom gv,
                          double* out) {
   __shared__ double red[32];
-  double s = 0.0;
-  NN4_FOR_NODES(gv) { s += (double)to_acc(z[row * gz.pitch + i]) * (double)q[row * gv.pitch + i]; }
-  block_sum_atomic(s, out, red);
+  using P = typename std::conditional<sizeof(TZ) == 8, double, float>::type;  // FP64 z: FP64 products
+  P s = 0;
+  NN4_FOR_NODES(gv) { s += (P)to_acc(z[row * gz.pitch + i]) * (P)q[row * gv.pitch + i]; }
+  block_sum_atomic((double)s, out, red);
 }
 
 // p = z - beta p_old with beta = zq / pq_old
@@ -65,23 +70,23 @@ __global__ void k_new_direction(const TZ* __restrict__ z, LevelGeom gz, const V*
   }
 }
 
-// alpha = pr / pq; x += alpha p; r -= alpha q; rT = r (if rT); norm += r^2
+// alpha = pr / pq; x += alpha p; r -= alpha q; rT = r (if rT); norm += r^2 (partial sums in V)
 template <typename V, typename TR>
 __global__ void k_fcg_update(V* __restrict__ x, V* __restrict__ r, const V* __restrict__ p,
                              const V* __restrict__ q, LevelGeom gv, TR* __restrict__ rT, LevelGeom gT,
                              const double* pr, const double* pq, double* norm2) {
   __shared__ double red[32];
   const V alpha = (V)(*pr / *pq);
-  double s = 0.0;
+  V s = 0;
   NN4_FOR_NODES(gv) {
     const long long o = row * gv.pitch + i;
     x[o] += alpha * p[o];
     const V rn = r[o] - alpha * q[o];
     r[o] = rn;
     if (rT) rT[row * gT.pitch + i] = from_acc<TR>(rn);
-    s += (double)rn * (double)rn;
+    s += rn * rn;
   }
-  block_sum_atomic(s, norm2, red);
+  block_sum_atomic((double)s, norm2, red);
 }
 
 // invd = 1 / (w c0 k - L k / 2): the diagonal of Eq. k-T (w = prod_d s_d / 2, c0 the interior

@@ -58,6 +58,8 @@ struct PlanImpl {
   double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *p64[2] = {nullptr, nullptr},
          *q64[2] = {nullptr, nullptr}, *k64 = nullptr;
   double *lk64 = nullptr, *invd64 = nullptr;  // L k and 1/diag(A) for Eq. k-T (FP64)
+  void* lkT = nullptr;      // L k in the inner storage type at the level-0 pitch
+  float* lk32 = nullptr;    // L k in FP32 for the inner Krylov mat-vec
   // inner flexible CG in FP32 vectors (opts.inner_krylov > 0): solution y, residual r, directions
   // p[2], q[2], coefficient k (FP32), all at the FP32 level-0 pitch
   LevelGeom g32;
@@ -323,9 +325,9 @@ PassArgs level_args(PlanImpl* P, int l, const void* b, void* out) {
   a.b = b;
   a.out = out;
   a.zchunk = L.cfg.zchunk;
-  if (P->vc && l == 0 && P->T == NN4_F64) {
-    a.lk = P->lk64;
-    a.invd = P->invd64;
+  if (P->vc && l == 0) {
+    a.lk = P->lkT;
+    a.invd = P->T == NN4_F64 ? P->invd64 : nullptr;
   }
   return a;
 }
@@ -486,6 +488,7 @@ int inner_krylov(PlanImpl* P, cudaStream_t s) {
     a.g = P->g32;
     a.L = L0.L;
     a.b = P->ri;
+    a.lk = P->vc ? P->lk32 : nullptr;
     a.out = P->qi[par];
     a.norm2 = P->scal + 9 + par;
     a.dot2 = P->scal + 11 + par;
@@ -639,6 +642,7 @@ int make_outer_maps(PlanImpl* P) {
     PassArgs b{};
     b.g = P->g32;
     b.b = P->ri;
+    b.lk = P->vc ? P->lk32 : nullptr;
     for (int t = 0; t < 2; ++t)
       ok = ok && make_pass_maps(&P->m_mat32[t], NN4_F32, b, P->cfg32, P->pi[t], P->vc ? P->k32 : nullptr);
   }
@@ -738,6 +742,7 @@ int autotune_plan(PlanImpl* P) {
     b.g = P->g32;
     b.L = P->lv[0].L;
     b.b = P->ri;
+    b.lk = P->vc ? P->lk32 : nullptr;
     b.out = P->qi[0];
     if ((rc = tune_pass(NN4_F32, OP_MATVEC, b, P->pi[1], P->vc ? P->k32 : nullptr, &P->cfg32, s))) return rc;
   }
@@ -1025,11 +1030,22 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
       destroy(P);
       return rc;
     }
+    // L k in the inner type (level-0 passes) and in FP32 (inner Krylov mat-vec)
+    if (P->T == NN4_F64) {
+      P->lkT = P->lk64;
+    } else if ((rc = alloc(P, &P->lkT, field_bytes(P->lv[0].g, P->T))) ||
+               (rc = launch_convert(NN4_F64, P->lk64, P->g64, P->T, P->lkT, P->lv[0].g, 0))) {
+      destroy(P);
+      return rc;
+    }
     if (o.inner_krylov > 0) {
       if (P->T == NN4_F32) {
         P->k32 = static_cast<float*>(P->lv[0].k);
+        P->lk32 = static_cast<float*>(P->lkT);
       } else if ((rc = alloc(P, (void**)&P->k32, field_bytes(P->g32, NN4_F32))) ||
-                 (rc = launch_convert(NN4_F64, P->k64, P->g64, NN4_F32, P->k32, P->g32, 0))) {
+                 (rc = launch_convert(NN4_F64, P->k64, P->g64, NN4_F32, P->k32, P->g32, 0)) ||
+                 (rc = alloc(P, (void**)&P->lk32, field_bytes(P->g32, NN4_F32))) ||
+                 (rc = launch_convert(NN4_F64, P->lk64, P->g64, NN4_F32, P->lk32, P->g32, 0))) {
         destroy(P);
         return rc;
       }

@@ -173,8 +173,14 @@ __global__ void __launch_bounds__(32 * WX * TYT)
   for (int t = 0; t < 8; ++t) c[t] = (A)a.L.c[t];
   const A wx = (A)half_count(ic, nx);
   A wy[RY];
+  unsigned dmask = 0;  // bit r: output row r lies on a Dirichlet face of x or y
 #pragma unroll
-  for (int r = 0; r < RY; ++r) wy[r] = wx * (A)half_count(min(jb + r, ny - 1), ny);
+  for (int r = 0; r < RY; ++r) {
+    const int j = min(jb + r, ny - 1);
+    wy[r] = wx * (A)half_count(j, ny);
+    const bool d = (g.dir[0] && i == 0) || (g.dir[1] && i == nx - 1) || (g.dir[2] && j == 0) || (g.dir[3] && j == ny - 1);
+    dmask |= (d ? 1u : 0u) << r;
+  }
 
   Runner<A, RY> sx, skx, sk;  // L~x, L~(kx), L~k
   sx.zero();
@@ -209,6 +215,7 @@ __global__ void __launch_bounds__(32 * WX * TYT)
     const int kout = zs + q - 2;  // output plane completed by this input plane
     if (q >= 2 && !failed) {
       const A wz = (A)half_count(kout, nz);
+      const bool dz = (g.dir[4] && kout == 0) || (g.dir[5] && kout == nz - 1);
 #pragma unroll
       for (int r = 0; r < RY; ++r) {
         const int j = jb + r;
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(32 * WX * TYT)
           if (OP == OP_APPLY) {
             out[idx] = from_acc<T>(Ax);
           } else {
-            const bool dirn = on_dirichlet(g, i, j, kout);
+            const bool dirn = dz || ((dmask >> r) & 1u);
             const A bv = to_acc(tb_[po]);
             if (OP == OP_RESIDUAL) {
               const A rv = dirn ? A(0) : bv - Ax;
@@ -247,7 +254,13 @@ __global__ void __launch_bounds__(32 * WX * TYT)
               nrm += (double)xc1[r] * (double)qv;
               dt2 += (double)xc1[r] * (double)bv;
             } else {
-              const A corr = use_invd ? (bv - Ax) * to_acc(ti_[po]) : (bv - Ax) / D;
+              A corr;
+              if (use_invd)
+                corr = (bv - Ax) * to_acc(ti_[po]);
+              else if constexpr (sizeof(A) == 4)
+                corr = __fdividef(bv - Ax, D);
+              else
+                corr = (bv - Ax) / D;
               const A xn = dirn ? xc1[r] : xc1[r] + (A)a.omega * corr;
               out[idx] = from_acc<T>(xn);
             }
@@ -336,8 +349,7 @@ template <typename T, int OP>
 int dispatch_vc(int vc, bool iso, const PassArgs& a, const PassCfg& cfg, const Maps& m, cudaStream_t st) {
   if (vc == 0) return dispatch_iso<T, OP, 0>(iso, a, cfg, m, st);
   if (vc == 1) return dispatch_iso<T, OP, 1>(iso, a, cfg, m, st);
-  if constexpr (sizeof(T) == 8) return dispatch_iso<T, OP, 2>(iso, a, cfg, m, st);
-  return set_error(NN4_EINVAL, "precomputed L k is supported for FP64 passes only");
+  return dispatch_iso<T, OP, 2>(iso, a, cfg, m, st);
 }
 
 template <typename T>

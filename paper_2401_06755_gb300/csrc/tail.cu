@@ -28,13 +28,16 @@ __device__ void tail_restrict(const TailLevel& F, const TailLevel& C) {
     const int I = t % C.g.nx, J = (t / C.g.nx) % C.g.ny, K = t / (C.g.nx * C.g.ny);
     A acc = A(0);
     if (!tdir(C.g, I, J, K)) {
+#pragma unroll
       for (int dz = -1; dz <= 1; ++dz) {
         const int k = 2 * K + dz;
         if (k < 0 || k >= F.g.nz) continue;
+#pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
           const int j = 2 * J + dy;
           if (j < 0 || j >= F.g.ny) continue;
           const A wyz = (dz ? A(0.5) : A(1)) * (dy ? A(0.5) : A(1));
+#pragma unroll
           for (int dx = -1; dx <= 1; ++dx) {
             const int i = 2 * I + dx;
             if (i < 0 || i >= F.g.nx) continue;
@@ -89,6 +92,7 @@ __device__ void tail_jacobi(const TailLevel& L, double omega) {
     }
     A s = A(0), D;
     if (a27) {
+#pragma unroll
       for (int d = 0; d < 27; ++d) {
         const int i2 = mirror(i + d % 3 - 1, g.nx), j2 = mirror(j + (d / 3) % 3 - 1, g.ny),
                   k2 = mirror(k + d / 9 - 1, g.nz);
@@ -96,6 +100,7 @@ __device__ void tail_jacobi(const TailLevel& L, double omega) {
       }
       D = to_acc(a27[13 * plane + o]);
     } else {
+#pragma unroll
       for (int d = 0; d < 27; ++d) {
         const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
         const int cls = (dx != 0) + 2 * (dy != 0) + 4 * (dz != 0);

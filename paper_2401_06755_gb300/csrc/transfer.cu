@@ -77,23 +77,23 @@ __global__ void k_prolong(const T* __restrict__ ec, T* ef, const T* base, const 
     return v * wxy;
   };
   const int k0 = blockIdx.z * kPz, k1 = min(gf.nz, k0 + kPz);
-  A lo = plane(k0 >> 1);
-  for (int k = k0; k < k1; ++k) {
+  // coarse planes k0/2 .. k0/2 + kPz/2 interpolated in-plane first (independent loads)
+  A cp[kPz / 2 + 1];
+  const int K0 = k0 >> 1;
+#pragma unroll
+  for (int t = 0; t <= kPz / 2; ++t) cp[t] = (K0 + t < gc.nz) ? plane(K0 + t) : A(0);
+#pragma unroll
+  for (int t = 0; t < kPz; ++t) {
+    const int k = k0 + t;
+    if (k >= k1) break;
+    const A v0 = (t & 1) ? A(0.5) * (cp[t >> 1] + cp[(t >> 1) + 1]) : cp[t >> 1];
     const long long idx = i + gf.pitch * ((long long)j + (long long)gf.ny * k);
-    A v;
-    if (k & 1) {
-      const A hi = plane((k >> 1) + 1);
-      v = A(0.5) * (lo + hi);
-      lo = hi;  // the next (even) fine plane injects coarse plane (k >> 1) + 1
-    } else {
-      v = lo;  // coarse plane k / 2 (set before the loop or by the previous odd plane)
-    }
     const bool dn = dxy || (gf.dir[4] && k == 0) || (gf.dir[5] && k == gf.nz - 1);
     if (dn) {
       ef[idx] = base ? base[idx] : from_acc<T>(A(0));
       continue;
     }
-    if (base) v += to_acc(base[idx]);
+    const A v = base ? v0 + to_acc(base[idx]) : v0;
     ef[idx] = from_acc<T>(v);
   }
 }

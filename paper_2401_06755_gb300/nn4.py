@@ -51,6 +51,12 @@ class _SolveInfo(ctypes.Structure):
                 ("kernels", ctypes.c_int64)]
 
 
+class _VOFParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("dt", "alpha_a", "eps_k", "K_plus", "K_minus", "beta", "eps_x",
+                                               "K_pos", "alpha_min", "alpha_max", "detect_hi", "detect_lo")] + \
+               [("p", ctypes.c_int32)]
+
+
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -88,6 +94,10 @@ def lib():
             "nn4_pressure_solve_host": (ctypes.c_int, [vp, vp, vp, dbl, i32, ctypes.POINTER(_SolveInfo), vp]),
             "nn4_plan_profile": (ctypes.c_int, [vp, ctypes.POINTER(_KernelTime), i32]),
             "nn4_plan_query": (ctypes.c_int, [vp, ctypes.POINTER(_PlanInfo)]),
+            "nn4_vof_params_default": (None, [ctypes.POINTER(_VOFParams), dbl]),
+            "nn4_vof_workspace_bytes": (ctypes.c_int64, [G]),
+            "nn4_vof_advect_residual": (ctypes.c_int, [G, ctypes.POINTER(_VOFParams), vp, vp, vp, vp, vp, vp, vp, vp]),
+            "nn4_mass_sum": (ctypes.c_int, [G, vp, vp, vp]),
             "nn4_last_error": (ctypes.c_char_p, []),
             "nn4_device_error": (ctypes.c_int, []),
             "nn4_version": (ctypes.c_char_p, []),
@@ -203,6 +213,38 @@ def jacobi_smooth(grid, b, x_in, k=None, x_out=None, omega=2.0 / 3.0, stream=Non
     _check(lib().nn4_jacobi_smooth(ctypes.byref(g), _dt(x_in), _ptr(b), _ptr(k), _ptr(x_in), _ptr(x_out),
                                    float(omega), _stream(stream)))
     return x_out
+
+
+def vof_params(dt, **over):
+    p = _VOFParams()
+    lib().nn4_vof_params_default(ctypes.byref(p), float(dt))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def vof_workspace(grid, device="cuda"):
+    n = lib().nn4_vof_workspace_bytes(ctypes.byref(grid.c(torch.float64)))
+    return torch.empty(int(n) // 8, dtype=torch.float64, device=device)
+
+
+def vof_advect_residual(grid, C, u, v, w, dt, s_C=None, C_next=None, workspace=None, params=None, stream=None):
+    """One explicit volume-fraction step; returns (s_C, C_next) (FP64 storage tensors)."""
+    s_C = torch.empty_like(C) if s_C is None else s_C
+    C_next = torch.empty_like(C) if C_next is None else C_next
+    workspace = vof_workspace(grid, C.device) if workspace is None else workspace
+    p = vof_params(dt) if params is None else params
+    g = grid.c(torch.float64)
+    _check(lib().nn4_vof_advect_residual(ctypes.byref(g), ctypes.byref(p), _ptr(C), _ptr(u), _ptr(v), _ptr(w),
+                                         _ptr(s_C), _ptr(C_next), _ptr(workspace), _stream(stream)))
+    return s_C, C_next
+
+
+def mass_sum(grid, C, out=None, stream=None):
+    out = torch.zeros(1, dtype=torch.float64, device=C.device) if out is None else out
+    g = grid.c(torch.float64)
+    _check(lib().nn4_mass_sum(ctypes.byref(g), _ptr(C), _ptr(out), _stream(stream)))
+    return out
 
 
 def device_error():
