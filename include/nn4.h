@@ -234,6 +234,23 @@ int nn4_vof_advect_residual(const nn4_grid* g, const nn4_vof_params* p, const do
                             const double* v, const double* w, double* s_C, double* C_next, void* workspace,
                             void* stream);
 
+/* The same volume-fraction step for callers that cannot allocate device memory: hosts that hand
+ * out all device memory from their own pool or fixed budget, and loops in which the implicit
+ * device synchronisation of cudaMalloc / cudaFree is not acceptable.  The paper has no
+ * counterpart; this is a deployment variant of nn4_vof_advect_residual.
+ * It takes no workspace: its 7-field scratch is a fixed device array inside the library
+ * (44 MiB, held by every GPU that loads the library until the process exits) and it calls no
+ * allocating routine.  Grids need pitch * ny * nz <= 786432 (e.g. 129 x 65 x 65 with the FP64
+ * pitch); larger grids return NN4_EINVAL with the limit in nn4_last_error().
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call, on every
+ * stream, shares the one array: calls that overlap on the GPU race on it and give wrong
+ * results, so serialise them (one stream, or events).  Each call writes every scratch element
+ * it reads, so no state carries over from the previous call.  Arguments and results as for
+ * nn4_vof_advect_residual. */
+int nn4_vof_advect_residual_static(const nn4_grid* g, const nn4_vof_params* p, const double* C, const double* u,
+                                   const double* v, const double* w, double* s_C, double* C_next, void* stream);
+
 /* *out (device FP64) = sum_i m_i C_i with m the lumped nodal volume: the C(t) of the mass
  * diagnostic (Section 3, mass conservation), accumulated in FP64. */
 int nn4_mass_sum(const nn4_grid* g, const double* C, double* out, void* stream);

@@ -5,6 +5,9 @@
 // part with 1.2 FP64 TFLOP/s), so they are plain one-thread-per-node kernels that read
 // neighbours through L1; every Q1 filter is applied sum-factorised with boundary-aware 1D
 // element factors (natural truncation).
+#include <mutex>
+#include <string>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -276,6 +279,59 @@ int nn4_vof_advect_residual(const nn4_grid* g, const nn4_vof_params* p, const do
   k_vof_coef<<<grd, blk, 0, s>>>(fg, *p, C, fx, fy, fz, ga, u, v, w, kx, ky, kz);
   k_vof_update<<<grd, blk, 0, s>>>(fg, *p, C, fx, fy, fz, kx, ky, kz, u, v, w, s_C, C_next);
   return check_cuda(cudaGetLastError(), "VOF kernels");
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+// The same three kernels with their scratch in a fixed device array instead of a caller buffer.
+// Every GPU that loads the library holds this array (44 MiB) until the process exits.
+constexpr long long kVofStaticFieldElems = 786432;  // max pitch * ny * nz per scratch field
+static __device__ __align__(256) double g_vof_scratch[7 * kVofStaticFieldElems];
+
+namespace {
+std::mutex g_vof_scratch_mu;
+double* g_vof_scratch_ptr[128] = {nullptr};  // device address of g_vof_scratch, per device ordinal
+}  // namespace
+
+int nn4_vof_advect_residual_static(const nn4_grid* g, const nn4_vof_params* p, const double* C, const double* u,
+                                   const double* v, const double* w, double* s_C, double* C_next, void* stream) {
+  int rc;
+  if ((rc = validate_grid(g, NN4_F64, 2)) || (rc = validate_ptr(C, "C")) || (rc = validate_ptr(u, "u")) ||
+      (rc = validate_ptr(v, "v")) || (rc = validate_ptr(w, "w")) || (rc = validate_ptr(s_C, "s_C")))
+    return rc;
+  if (!p) return set_error(NN4_EINVAL, "params is NULL");
+  if (!(p->dt > 0.0) || p->p < 1 || p->p > 3) return set_error(NN4_EINVAL, "bad VOF parameters");
+  if (C_next && (rc = validate_ptr(C_next, "C_next"))) return rc;
+  if (s_C == C || C_next == C) return set_error(NN4_EINVAL, "outputs must not alias C");
+  const long long f = (long long)g->pitch * g->n[1] * g->n[2];
+  if (f > kVofStaticFieldElems)
+    return set_error(NN4_EINVAL, "grid too large for the static scratch: pitch * ny * nz = " + std::to_string(f) +
+                                     " > " + std::to_string(kVofStaticFieldElems));
+  // set-up once per device, with that device current: the host-side name of the array is not a
+  // device address, so take the address from the runtime
+  int dev = 0;
+  if ((rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice"))) return rc;
+  if (dev < 0 || dev >= 128) return set_error(NN4_EUNSUPPORTED, "device ordinal out of range");
+  double* ws = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_vof_scratch_mu);
+    if (!g_vof_scratch_ptr[dev]) {
+      void* ptr = nullptr;
+      if ((rc = check_cuda(cudaGetSymbolAddress(&ptr, g_vof_scratch), "cudaGetSymbolAddress(scratch)"))) return rc;
+      g_vof_scratch_ptr[dev] = static_cast<double*>(ptr);
+    }
+    ws = g_vof_scratch_ptr[dev];
+  }
+  // every scratch element the kernels read is written earlier in the same call (all nodes of the
+  // seven fields), so nothing needs clearing between calls
+  const FlowGeom fg = flow_geom(g);
+  double *fx = ws, *fy = ws + f, *fz = ws + 2 * f, *ga = ws + 3 * f, *kx = ws + 4 * f, *ky = ws + 5 * f,
+         *kz = ws + 6 * f;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  dim3 blk(32, 4), grd((fg.nx + 31) / 32, (fg.ny + 3) / 4, fg.nz);
+  k_vof_grad<<<grd, blk, 0, s>>>(fg, C, u, v, w, fx, fy, fz, ga);
+  k_vof_coef<<<grd, blk, 0, s>>>(fg, *p, C, fx, fy, fz, ga, u, v, w, kx, ky, kz);
+  k_vof_update<<<grd, blk, 0, s>>>(fg, *p, C, fx, fy, fz, kx, ky, kz, u, v, w, s_C, C_next);
+  return check_cuda(cudaGetLastError(), "VOF kernels (static scratch)");
 }
 
 int nn4_mass_sum(const nn4_grid* g, const double* C, double* out, void* stream) {
