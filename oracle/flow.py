@@ -117,3 +117,143 @@ def vof_step(shape, h, C, u, v, w, dt, prm=VOFParams()):
     parts = {"grad": Cd, "a_C": a_C, "k_abs": k_abs, "S": S, "w_plus": w_plus, "w_minus": w_minus,
              "k_neg": k_neg, "k": kd}
     return s_C, C_next, parts
+
+
+# ---------------------------------------------------------------- Navier-Stokes terms
+
+@dataclass(frozen=True)
+class FlowParams:
+    """Physical constants of one run (Sections 2.1, 2.3.2, 2.3.5) and the momentum scheme's."""
+    rho_l: float = 1000.0
+    rho_g: float = 1.0
+    mu_l: float = 1e-3
+    mu_g: float = 1.8e-5
+    sigma_t: float = 0.07          # surface tension coefficient
+    g: float = 9.81                # gravity magnitude, acting along -z
+    alpha_a: float = 2.0           # Eq. a_psi
+    p: int = 1
+    eps_k: float = 1e-7            # Eqs. k-abs, h_Psi, k-square
+
+    @property
+    def alpha_kabs(self):
+        return 1.0 / (8.0 * 2 ** self.p)
+
+    @property
+    def alpha_ksquare(self):
+        return 8.0 / 2 ** self.p
+
+
+def density(C, prm):
+    """Eq. density-n: rho = rho_l C + rho_g (1 - C)."""
+    return prm.rho_l * C + prm.rho_g * (1.0 - C)
+
+
+def viscosity(C, prm):
+    """mu = mu_l C + mu_g (1 - C) (reading: the paper's scalar mu, made two-phase)."""
+    return prm.mu_l * C + prm.mu_g * (1.0 - C)
+
+
+def _filters(shape, h):
+    ei = fem.element_integrals(h)
+    m = fem.lumped_mass(shape, h)
+    return ei, m
+
+
+def pointwise_gradient(shape, h, f):
+    """m^-1 f(f; w_d), d = x, y, z."""
+    ei, m = _filters(shape, h)
+    return [fem.apply_assembled(ei["grad"][d], f) / m for d in range(3)]
+
+
+def surface_tension(shape, h, C, prm):
+    """Eqs. surface-tension-k and surface-tension-uvw: n = grad C / (eps_t + |grad C|),
+    kappa = m^-1 sum_d f(n_d; w_d) (the printed w_v of the z term read as w_z),
+    s_t = sigma_t kappa grad C; eps_t = 1e-7 / h with h the smallest spacing (reading)."""
+    ei, m = _filters(shape, h)
+    Cd = pointwise_gradient(shape, h, C)
+    eps_t = 1e-7 / min(h)
+    norm = np.sqrt(Cd[0] ** 2 + Cd[1] ** 2 + Cd[2] ** 2)
+    nd = [Cd[d] / (eps_t + norm) for d in range(3)]
+    kappa = sum(fem.apply_assembled(ei["grad"][d], nd[d]) for d in range(3)) / m
+    return [prm.sigma_t * kappa * Cd[d] for d in range(3)], kappa
+
+
+def pressure_rhs_hydrostatic(shape, h, C, prm, dirichlet_mask=None):
+    """Stage 1 (Eq. hydro-pressure / Eq. ph_disc): the weak form int grad N . (s_q + s_t) with
+    s_q = -rho g e_z, i.e. b = sum_d G_d^T s_d (G_d the assembled first-derivative filter w_d).
+    With A the weak -laplacian this gives dp/dn = s.n on natural faces (the bottom condition
+    dp_hs/dz = -rho g of Section 2.3.3)."""
+    ei, _ = _filters(shape, h)
+    st, _ = surface_tension(shape, h, C, prm)
+    s = [st[0], st[1], st[2] - prm.g * density(C, prm)]
+    b = sum(fem.apply_assembled(ei["grad"][d].T, s[d]) for d in range(3))
+    if dirichlet_mask is not None:
+        b = np.where(dirichlet_mask, 0.0, b)
+    return b
+
+
+def pressure_rhs_correction(shape, h, rho, ut, dt, dirichlet_mask=None):
+    """Stage 3 (Eq. ph_disc2): b = -(1/dt) [ sum_d f(rho u~_d; w_d) - sum_d u~_d f(rho; w_d) ]."""
+    ei, _ = _filters(shape, h)
+    b = np.zeros(shape)
+    for d in range(3):
+        G = ei["grad"][d]
+        b -= (fem.apply_assembled(G, rho * ut[d]) - ut[d] * fem.apply_assembled(G, rho)) / dt
+    if dirichlet_mask is not None:
+        b = np.where(dirichlet_mask, 0.0, b)
+    return b
+
+
+def velocity_correction(shape, h, rho, dp, dt, wall_mask=None):
+    """Eq. vel-cor: du_d = -dt m^-1 f(dp; w_d) / rho (zero on no-slip walls)."""
+    ei, m = _filters(shape, h)
+    out = []
+    for d in range(3):
+        du = -dt * fem.apply_assembled(ei["grad"][d], dp) / (m * rho)
+        if wall_mask is not None:
+            du = np.where(wall_mask, 0.0, du)
+        out.append(du)
+    return out
+
+
+def momentum_predict(shape, h, C, un, uh, p_total, dt, prm, wall_mask=None):
+    """One Stage-2 iteration (Eqs. Petrov-u/v/w, k_Psi-n, k-abs, k-square, max-k, velocity-1).
+
+    un: velocity at level n; uh: the current u^{n+1/2}; p_total = p_hs + p_nh.  For each component
+    Psi:  s~ = rho (u.grad_raw Psi) + f^lap(Psi, k_Psi; w_lap) + f(p; w_d) - f(s_Psi + s_tPsi; w_m),
+    with k_Psi = rho min(k_max, k_abs, k_square) + mu computed from u^{n+1/2} (reading), then
+    Psi~ = Psi^n - dt s~ / (m rho) (sigma = 0).  Returns (u~, u^{n+1/2} = (u^n + u~) / 2).
+    """
+    ei, m = _filters(shape, h)
+    rho = density(C, prm)
+    mu = viscosity(C, prm)
+    st, _ = surface_tension(shape, h, C, prm)
+    src = [st[0], st[1], st[2] - prm.g * rho]          # s_Psi + s_tPsi (buoyancy on w only)
+    L = ei["stiff"]
+    kmax = h[0] * np.abs(uh[0]) + h[1] * np.abs(uh[1]) + h[2] * np.abs(uh[2])   # Eq. max-k
+    ut = []
+    for c in range(3):
+        psi = uh[c]
+        raw = [fem.apply_assembled(ei["grad"][d], psi) for d in range(3)]
+        pd = [raw[d] / m for d in range(3)]
+        gpsi = uh[0] * pd[0] + uh[1] * pd[1] + uh[2] * pd[2]
+        a = prm.alpha_a * (fem.apply_assembled(ei["mass"], gpsi) / m - gpsi)        # Eq. a_psi
+        ab = [np.abs(q) for q in pd]
+        sab = ab[0] + ab[1] + ab[2]
+        hsum = h[0] * ab[0] + h[1] * ab[1] + h[2] * ab[2]
+        k_abs = prm.alpha_kabs * np.abs(a) * hsum / (prm.eps_k + sab ** 2 / 3.0)   # Eq. efficient-kabs
+        h_psi = hsum / (prm.eps_k + sab)                                             # Eq. h_Psi
+        k_sq = (prm.alpha_ksquare * a * a * h_psi /
+                (prm.eps_k + (np.abs(uh[0] * pd[0]) + np.abs(uh[1] * pd[1]) + np.abs(uh[2] * pd[2]))
+                 * (pd[0] ** 2 + pd[1] ** 2 + pd[2] ** 2) / 3.0))                   # Eq. k-square
+        k = rho * np.minimum(kmax, np.minimum(k_abs, k_sq)) + mu                     # Eq. k_Psi-n
+        s = rho * (uh[0] * raw[0] + uh[1] * raw[1] + uh[2] * raw[2])
+        s = s + 0.5 * (fem.apply_assembled(L, k * psi) + k * fem.apply_assembled(L, psi)
+                       - psi * fem.apply_assembled(L, k))                            # Eq. k-T
+        s = s + fem.apply_assembled(ei["grad"][c], p_total)
+        s = s - fem.apply_assembled(ei["mass"], src[c])
+        u_new = un[c] - dt * s / (m * rho)                                           # Eq. velocity-1
+        if wall_mask is not None:
+            u_new = np.where(wall_mask, 0.0, u_new)
+        ut.append(u_new)
+    return ut, [0.5 * (un[c] + ut[c]) for c in range(3)]

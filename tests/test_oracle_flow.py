@@ -95,3 +95,60 @@ def test_pure_advection_of_smooth_field_is_consistent():
         inner = (slice(3, -3),) * 3
         errs.append(np.abs((C - Cn)[inner] / dt - exact_rate[inner]).max())
     assert errs[1] < errs[0] / 2.5
+
+
+def test_hydrostatic_column_is_exact():
+    """Uniform density, no surface tension: the Stage-1 solve gives p = rho g (L - z) exactly
+    (a linear field lies in the Q1 space; the natural bottom row imposes dp/dz = -rho g)."""
+    from oracle import direct, mg
+    n, h = (5, 5, 9), (0.25, 0.25, 0.125)
+    g = mg.Grid(n, h, (False,) * 5 + (True,))
+    prm = flow.FlowParams(sigma_t=0.0)
+    C = np.full(g.shape, 1.0)
+    b = flow.pressure_rhs_hydrostatic(g.shape, h, C, prm, mg.dirichlet_mask(g))
+    p = direct.solve_dense(g, b)
+    _, _, z = node_coords(n, h)
+    np.testing.assert_allclose(p, prm.rho_l * prm.g * (z.max() - z), atol=1e-10)
+
+
+def test_surface_tension_of_a_plane_interface_vanishes():
+    """A planar interface (C linear in x) has zero curvature at interior nodes."""
+    n, h = (9, 6, 6), (0.1, 0.1, 0.1)
+    x, _, _ = node_coords(n, h)
+    C = np.clip(0.2 + x, 0, 1)
+    st, kappa = flow.surface_tension(C.shape, h, C, flow.FlowParams())
+    assert np.abs(kappa[1:-1, 1:-1, 1:-1]).max() < 1e-8
+
+
+def test_correction_rhs_vanishes_for_divergence_free_uniform_density():
+    """Uniform rho and a divergence-free u~ = (y, -x, 0): the Stage-3 RHS is zero inside
+    (the two filter terms cancel exactly for uniform rho; div u~ = 0)."""
+    n, h = (7, 7, 7), (0.1, 0.1, 0.1)
+    x, y, _ = node_coords(n, h)
+    rho = np.full(x.shape, 3.0)
+    b = flow.pressure_rhs_correction(x.shape, h, rho, [y, -x, np.zeros_like(x)], 1e-3)
+    assert np.abs(b[1:-1, 1:-1, 1:-1]).max() < 1e-10
+
+
+def test_velocity_correction_of_linear_pressure():
+    """dp = a x: du = -dt a / rho at interior nodes, dv = dw = 0."""
+    n, h = (7, 6, 5), (0.2, 0.1, 0.3)
+    x, _, _ = node_coords(n, h)
+    rho = np.full(x.shape, 2.0)
+    du = flow.velocity_correction(x.shape, h, rho, 4.0 * x, 0.01)
+    np.testing.assert_allclose(du[0][1:-1, 1:-1, 1:-1], -0.01 * 4.0 / 2.0, rtol=1e-12)
+    assert np.abs(du[1]).max() < 1e-13 and np.abs(du[2]).max() < 1e-13
+
+
+def test_momentum_at_rest_in_hydrostatic_balance():
+    """Fluid at rest with p = rho g (L - z) and uniform rho: buoyancy and pressure gradient
+    cancel at interior nodes, so u~ = 0 there (s_w = -g rho against f(p; w_z))."""
+    n, h = (6, 6, 9), (0.2, 0.2, 0.125)
+    _, _, z = node_coords(n, h)
+    prm = flow.FlowParams(sigma_t=0.0, mu_l=1e-3)
+    C = np.ones(z.shape)
+    p = prm.rho_l * prm.g * (z.max() - z)
+    zero = [np.zeros(z.shape)] * 3
+    ut, uh = flow.momentum_predict(z.shape, h, C, zero, zero, p, 1e-3, prm)
+    for c in range(3):
+        assert np.abs(ut[c][1:-1, 1:-1, 1:-1]).max() < 1e-9
