@@ -72,6 +72,23 @@ struct PassMaps {
   CUtensorMap x, k, b, lk, invd;
 };
 
+// One instance's part of a batched stencil pass (device table entry, 64-byte aligned maps).
+struct alignas(64) BatchPass {
+  PassMaps maps;
+  PassArgs args;
+  int inst;      // instance index (for the active flags)
+  int first;     // index of this instance's first work item
+  int tiles_x, tiles_y;
+};
+
+// Batched stencil pass over `count` instances (constant coefficient, default tile shape); `items`
+// is a device array; `active` (device, nullable) skips converged instances.
+int launch_pass_batch(nn4_dtype dt, int op, const BatchPass* items, int count, int total, const int* active,
+                      cudaStream_t s);
+// Fills the tiling fields of a batch entry for the default tile shape (returns its item count).
+int batch_pass_tiles(nn4_dtype dt, BatchPass* bp);
+PassCfg batch_pass_cfg(nn4_dtype dt);
+
 // stencil.cu: constant coefficient (k == nullptr) or Eq. k-T (k given).  Every input is read with
 // TMA; the maps are built here unless `maps` is given (built with make_pass_maps for this cfg).
 int launch_pass(nn4_dtype dt, int op, const PassArgs& a, const void* x, const void* k,
@@ -123,5 +140,20 @@ struct TailArgs {
 };
 
 int launch_tail(nn4_dtype dt, const TailArgs& a, cudaStream_t s);
+// One CTA per instance (tab: device array of `count` tails; `active` skips converged ones).
+int launch_tail_batch(nn4_dtype dt, const TailArgs* tab, int count, const int* active, cudaStream_t s);
+
+// Batched restriction (src = fine r, dst = coarse r) or prolongation (src = coarse e, dst = fine
+// t, optional base) over instances; device table entries.
+struct BatchXfer {
+  LevelGeom gf, gc;
+  const void* src;
+  void* dst;
+  const void* base;
+  int inst, first, bx, by;
+};
+int batch_xfer_blocks(BatchXfer* X, bool prolong);
+int launch_xfer_batch(nn4_dtype dt, bool prolong, const BatchXfer* tab, int count, int total, const int* active,
+                      cudaStream_t s);
 
 }  // namespace nn4

@@ -15,6 +15,8 @@
 //     sums p01, p11 of those; across planes the z-neighbour sums.  Output k then needs
 //     u(k-1) + v(k) + u(k+1) with u = sum c_ab1 p_ab and v = sum c_ab0 p_ab, kept as two running
 //     partial sums in registers (about 14 operations per node and field).
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -89,8 +91,25 @@ struct Maps {
 };
 
 template <typename T, int OP, int VC, bool ISO, int WX, int RY, int TYT, int S>
-__global__ void __launch_bounds__(32 * WX * TYT)
-    k_pass(const __grid_constant__ Maps maps, const PassArgs a) {
+struct PassLayout {
+  static constexpr int AL = kAlign<T>;
+  static constexpr int TX = 32 * WX, TY = TYT * RY;
+  static constexpr int NF = VC ? 2 : 1;
+  static constexpr bool HAS_B = OP != OP_APPLY;
+  static constexpr int HALO_PAD = ((TX + 2 * AL) * (TY + 2) * (int)sizeof(T) + 127) / 128 * 128;
+  static constexpr int PT_PAD = (TX * TY * (int)sizeof(T) + 127) / 128 * 128;
+  static constexpr int NP = (HAS_B ? 1 : 0) + (VC == 2 ? 2 : 0);
+  static constexpr int STAGE = NF * HALO_PAD + NP * PT_PAD;
+  static constexpr size_t SMEM = (size_t)S * STAGE + S * 8 + 32 * 8;
+};
+
+// One output tile (tbx, tby) x z-chunk tbz of a stencil pass.  `qb` counts the planes this CTA has
+// consumed before (stage = (qb + q) % S, phase parity from (qb + q) / S), so a CTA can run several
+// tiles in a row on the same barriers.  Returns false if a bounded wait gave up.
+template <typename T, int OP, int VC, bool ISO, int WX, int RY, int TYT, int S>
+__device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int tbx, int tby, int tbz,
+                                          unsigned& qb) {
+  const Maps& maps = *mp;
   using A = typename Acc<T>::type;
   constexpr int AL = kAlign<T>;
   constexpr int TX = 32 * WX, TY = TYT * RY;
@@ -107,11 +126,12 @@ __global__ void __launch_bounds__(32 * WX * TYT)
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * STAGE);
   double* red = reinterpret_cast<double*>(bars + S);
+  const unsigned q0 = qb;
 
   const LevelGeom& g = a.g;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int zs = blockIdx.z * a.zchunk;
+  const int x0 = tbx * TX, y0 = tby * TY;
+  const int zs = tbz * a.zchunk;
   const int ze = min(nz, zs + a.zchunk);
   const int tid = threadIdx.x + TX * threadIdx.y;
   const int nplanes = ze - zs + 2;  // input planes zs-1 .. ze
@@ -122,14 +142,10 @@ __global__ void __launch_bounds__(32 * WX * TYT)
     prefetch_tmap(&maps.x);
     if (VC) prefetch_tmap(&maps.k);
     if (HAS_B) prefetch_tmap(&maps.b);
-#pragma unroll
-    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
-    fence_barrier_init();
   }
-  __syncthreads();
 
   auto issue = [&](int q) {
-    const int s = q % S;
+    const int s = (q0 + q) % S;
     unsigned char* st = smem + s * STAGE;
     const int zp = mirror(zs - 1 + q, nz);
     const int kout = zs + q - 2;
@@ -194,8 +210,8 @@ __global__ void __launch_bounds__(32 * WX * TYT)
   T* out = reinterpret_cast<T*>(a.out);
 
   for (int q = 0; q < nplanes; ++q) {
-    const int s = q % S;
-    if (!mbar_wait_bounded(&bars[s], (uint32_t)((q / S) & 1))) failed = true;
+    const int s = (q0 + q) % S;
+    if (!mbar_wait_bounded(&bars[s], (uint32_t)(((q0 + q) / S) & 1))) failed = true;
     const unsigned char* st = smem + s * STAGE;
     const T* tx_ = reinterpret_cast<const T*>(st);
     const T* tk_ = reinterpret_cast<const T*>(st + HALO_PAD);
@@ -291,27 +307,70 @@ __global__ void __launch_bounds__(32 * WX * TYT)
     }
     if (tid == 0 && q + S < nplanes) issue(q + S);
   }
+  qb = q0 + nplanes;
   if (failed) {
     // drain copies that may still be in flight before the CTA exits
     if (tid == 0) {
       for (int q = 0; q < min(S, nplanes); ++q) mbar_wait_bounded(&bars[q], 0u);
     }
     __syncthreads();
-    return;
+    return false;
   }
   if ((OP == OP_RESIDUAL || OP == OP_MATVEC) && a.norm2 != nullptr) block_sum_atomic(nrm, a.norm2, red);
   if (OP == OP_MATVEC && a.dot2 != nullptr) block_sum_atomic(dt2, a.dot2, red);
+  __syncthreads();  // stage buffers are free for the next tile
+  return true;
+}
+
+template <typename T, int OP, int VC, bool ISO, int WX, int RY, int TYT, int S>
+__device__ __forceinline__ void init_bars() {
+  using Lay = PassLayout<T, OP, VC, ISO, WX, RY, TYT, S>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * Lay::STAGE);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+}
+
+template <typename T, int OP, int VC, bool ISO, int WX, int RY, int TYT, int S>
+__global__ void __launch_bounds__(32 * WX * TYT) k_pass(const __grid_constant__ Maps maps, const PassArgs a) {
+  init_bars<T, OP, VC, ISO, WX, RY, TYT, S>();
+  unsigned qb = 0;
+  pass_tile<T, OP, VC, ISO, WX, RY, TYT, S>(&maps, a, blockIdx.x, blockIdx.y, blockIdx.z, qb);
+}
+
+// Batched form: one launch over the tiles of many independent instances.  Item t of instance i
+// is tile (t % tiles_x, (t / tiles_x) % tiles_y, t / (tiles_x tiles_y)); CTAs stride over all
+// items (persistent), skipping instances whose `active` flag is 0.
+template <typename T, int OP, int VC, bool ISO, int WX, int RY, int TYT, int S>
+__global__ void __launch_bounds__(32 * WX * TYT)
+    k_pass_batch(const BatchPass* __restrict__ items, int count, int total, const int* __restrict__ active) {
+  init_bars<T, OP, VC, ISO, WX, RY, TYT, S>();
+  unsigned qb = 0;
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    int lo = 0, hi = count - 1;  // last instance whose first item is <= it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].first <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchPass& bp = items[lo];
+    if (active && !active[bp.inst]) continue;
+    const int t = it - bp.first;
+    if (!pass_tile<T, OP, VC, ISO, WX, RY, TYT, S>(reinterpret_cast<const Maps*>(&bp.maps), bp.args,
+                                                   t % bp.tiles_x, (t / bp.tiles_x) % bp.tiles_y,
+                                                   t / (bp.tiles_x * bp.tiles_y), qb))
+      return;
+  }
 }
 
 template <typename T, int OP, int VC, bool ISO, int WX, int RY, int TYT, int S>
 int launch_t(const PassArgs& a, const Maps& maps, cudaStream_t st) {
-  constexpr int AL = kAlign<T>;
   constexpr int TX = 32 * WX, TY = TYT * RY;
-  constexpr int NF = VC ? 2 : 1;
-  constexpr int HALO_PAD = ((TX + 2 * AL) * (TY + 2) * (int)sizeof(T) + 127) / 128 * 128;
-  constexpr int PT_PAD = (TX * TY * (int)sizeof(T) + 127) / 128 * 128;
-  constexpr int NP = (OP != OP_APPLY ? 1 : 0) + (VC == 2 ? 2 : 0);
-  const size_t smem = (size_t)S * (NF * HALO_PAD + NP * PT_PAD) + S * 8 + 32 * 8;
+  const size_t smem = PassLayout<T, OP, VC, ISO, WX, RY, TYT, S>::SMEM;
   auto kern = k_pass<T, OP, VC, ISO, WX, RY, TYT, S>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -364,7 +423,54 @@ int dispatch_op(int op, int vc, const PassArgs& a, const PassCfg& cfg, const Map
   return set_error(NN4_EINVAL, "bad stencil op");
 }
 
+template <typename T, int OP, bool ISO>
+int launch_batch_t(const BatchPass* items, int count, int total, const int* active, cudaStream_t st) {
+  using Lay = PassLayout<T, OP, 0, ISO, 1, 4, 4, 3>;
+  auto kern = k_pass_batch<T, OP, 0, ISO, 1, 4, 4, 3>;
+  const size_t smem = Lay::SMEM;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(batched pass)");
+  }
+  const int grid = std::min(total, 152 * 8);
+  kern<<<grid, dim3(32, 4), smem, st>>>(items, count, total, active);
+  return check_cuda(cudaGetLastError(), "batched stencil pass launch");
+}
+
 }  // namespace
+
+PassCfg batch_pass_cfg(nn4_dtype dt) {
+  PassCfg c;
+  c.wx = 1;
+  c.ry = 4;
+  c.tyt = 4;
+  c.stages = 3;
+  c.zchunk = 0;
+  return c;
+}
+
+int batch_pass_tiles(nn4_dtype, BatchPass* bp) {
+  const LevelGeom& g = bp->args.g;
+  bp->tiles_x = (g.nx + 31) / 32;
+  bp->tiles_y = (g.ny + 15) / 16;
+  const int tz = (g.nz + bp->args.zchunk - 1) / bp->args.zchunk;
+  return bp->tiles_x * bp->tiles_y * tz;
+}
+
+int launch_pass_batch(nn4_dtype dt, int op, const BatchPass* items, int count, int total, const int* active,
+                      cudaStream_t s) {
+  if (total <= 0) return NN4_OK;
+  // every instance of a batch has equal spacing per axis (checked at batch creation)
+  switch (dt * 4 + op) {
+    case NN4_F64 * 4 + OP_RESIDUAL: return launch_batch_t<double, OP_RESIDUAL, true>(items, count, total, active, s);
+    case NN4_F64 * 4 + OP_JACOBI: return launch_batch_t<double, OP_JACOBI, true>(items, count, total, active, s);
+    case NN4_F32 * 4 + OP_RESIDUAL: return launch_batch_t<float, OP_RESIDUAL, true>(items, count, total, active, s);
+    case NN4_F32 * 4 + OP_JACOBI: return launch_batch_t<float, OP_JACOBI, true>(items, count, total, active, s);
+    case NN4_BF16 * 4 + OP_RESIDUAL: return launch_batch_t<bf16, OP_RESIDUAL, true>(items, count, total, active, s);
+    case NN4_BF16 * 4 + OP_JACOBI: return launch_batch_t<bf16, OP_JACOBI, true>(items, count, total, active, s);
+  }
+  return set_error(NN4_EINVAL, "unsupported batched pass");
+}
 
 PassCfg default_pass_cfg(nn4_dtype dt, bool vc, const LevelGeom& g) {
   PassCfg c;

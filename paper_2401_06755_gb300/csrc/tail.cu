@@ -1,6 +1,6 @@
 // The coarse tail of the sawtooth V-cycle in one launch.  Levels with few nodes cannot fill the
 // GPU and every separate launch costs several microseconds of latency, so all levels at or below
-// a few thousand nodes run in a single CTA: restriction down to the coarsest level, the dense
+// a few hundred nodes run in a single CTA: restriction down to the coarsest level, the dense
 // coarsest solve, then prolongation and one Jacobi sweep per level back up to the entry level
 // (Section 2.4, multigrid figure: the same steps the per-level kernels perform).
 #include "common.cuh"
@@ -152,7 +152,35 @@ __global__ void __launch_bounds__(1024) k_tail(const TailArgs a) {
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(1024) k_tail_batch(const TailArgs* __restrict__ tab, const int* __restrict__ active) {
+  if (active && !active[blockIdx.x]) return;
+  const TailArgs& a = tab[blockIdx.x];
+  for (int l = 0; l + 1 < a.nlev; ++l) {
+    tail_restrict<T>(a.lv[l], a.lv[l + 1]);
+    __syncthreads();
+  }
+  tail_coarsest<T>(a);
+  __syncthreads();
+  for (int l = a.nlev - 2; l >= 0; --l) {
+    tail_prolong<T>(a.lv[l + 1], a.lv[l]);
+    __syncthreads();
+    tail_jacobi<T>(a.lv[l], a.omega);
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+int launch_tail_batch(nn4_dtype dt, const TailArgs* tab, int count, const int* active, cudaStream_t s) {
+  if (count <= 0) return NN4_OK;
+  switch (dt) {
+    case NN4_F64: k_tail_batch<double><<<count, 1024, 0, s>>>(tab, active); break;
+    case NN4_F32: k_tail_batch<float><<<count, 1024, 0, s>>>(tab, active); break;
+    case NN4_BF16: k_tail_batch<bf16><<<count, 1024, 0, s>>>(tab, active); break;
+  }
+  return check_cuda(cudaGetLastError(), "batched coarse tail launch");
+}
 
 int launch_tail(nn4_dtype dt, const TailArgs& a, cudaStream_t s) {
   if (a.nlev < 1 || a.nlev > kMaxTail || a.nfree > 1024) return set_error(NN4_EINVAL, "bad coarse tail");

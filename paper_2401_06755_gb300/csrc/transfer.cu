@@ -98,6 +98,106 @@ __global__ void k_prolong(const T* __restrict__ ec, T* ef, const T* base, const 
   }
 }
 
+// Batched transfers: CTA b handles block (b - first) of instance entry `lo` (a grid of 32 x 4
+// thread blocks over (x, y) times z-blocks).
+template <typename T>
+__global__ void k_restrict_batch(const BatchXfer* __restrict__ tab, int count, int total, const int* __restrict__ active) {
+  using A = typename Acc<T>::type;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].first <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchXfer& X = tab[lo];
+  if (active && !active[X.inst]) return;
+  const int b = blockIdx.x - X.first;
+  const int I = (b % X.bx) * 32 + threadIdx.x;
+  const int J = ((b / X.bx) % X.by) * 4 + threadIdx.y;
+  const int K = b / (X.bx * X.by);
+  const LevelGeom &gf = X.gf, &gc = X.gc;
+  if (I >= gc.nx || J >= gc.ny) return;
+  const T* rf = static_cast<const T*>(X.src);
+  A acc = A(0);
+  if (!dir_node(gc, I, J, K)) {
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int k = 2 * K + dz;
+      if (k < 0 || k >= gf.nz) continue;
+      A az = A(0);
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int j = 2 * J + dy;
+        if (j < 0 || j >= gf.ny) continue;
+        const T* row = rf + gf.pitch * ((long long)j + (long long)gf.ny * k);
+        const int i = 2 * I;
+        A ax = to_acc(row[i]);
+        if (i > 0) ax += A(0.5) * to_acc(row[i - 1]);
+        if (i + 1 < gf.nx) ax += A(0.5) * to_acc(row[i + 1]);
+        az += (dy == 0 ? A(1) : A(0.5)) * ax;
+      }
+      acc += (dz == 0 ? A(1) : A(0.5)) * az;
+    }
+  }
+  static_cast<T*>(X.dst)[I + gc.pitch * ((long long)J + (long long)gc.ny * K)] = from_acc<T>(acc);
+}
+
+template <typename T>
+__global__ void k_prolong_batch(const BatchXfer* __restrict__ tab, int count, int total, const int* __restrict__ active) {
+  using A = typename Acc<T>::type;
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].first <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchXfer& X = tab[lo];
+  if (active && !active[X.inst]) return;
+  const int b = blockIdx.x - X.first;
+  const LevelGeom &gf = X.gf, &gc = X.gc;
+  const int i = (b % X.bx) * 32 + threadIdx.x;
+  const int j = ((b / X.bx) % X.by) * 4 + threadIdx.y;
+  const int kb = b / (X.bx * X.by);
+  if (i >= gf.nx || j >= gf.ny) return;
+  const T* ec = static_cast<const T*>(X.src);
+  T* ef = static_cast<T*>(X.dst);
+  const T* base = static_cast<const T*>(X.base);
+  const int I0 = i >> 1, J0 = j >> 1;
+  const int I1 = I0 + (i & 1), J1 = J0 + (j & 1);
+  const A wxy = ((i & 1) ? A(0.5) : A(1)) * ((j & 1) ? A(0.5) : A(1));
+  const bool dxy = (gf.dir[0] && i == 0) || (gf.dir[1] && i == gf.nx - 1) || (gf.dir[2] && j == 0) ||
+                   (gf.dir[3] && j == gf.ny - 1);
+  auto plane = [&](int K) {
+    const T* p = ec + gc.pitch * (long long)gc.ny * K;
+    A v = to_acc(p[I0 + gc.pitch * (long long)J0]);
+    if (i & 1) v += to_acc(p[I1 + gc.pitch * (long long)J0]);
+    if (j & 1) {
+      A t = to_acc(p[I0 + gc.pitch * (long long)J1]);
+      if (i & 1) t += to_acc(p[I1 + gc.pitch * (long long)J1]);
+      v += t;
+    }
+    return v * wxy;
+  };
+  const int k0 = kb * kPz, k1 = min(gf.nz, k0 + kPz);
+  A cp[kPz / 2 + 1];
+  const int K0 = k0 >> 1;
+#pragma unroll
+  for (int t = 0; t <= kPz / 2; ++t) cp[t] = (K0 + t < gc.nz) ? plane(K0 + t) : A(0);
+#pragma unroll
+  for (int t = 0; t < kPz; ++t) {
+    const int k = k0 + t;
+    if (k >= k1) break;
+    const A v0 = (t & 1) ? A(0.5) * (cp[t >> 1] + cp[(t >> 1) + 1]) : cp[t >> 1];
+    const long long idx = i + gf.pitch * ((long long)j + (long long)gf.ny * k);
+    const bool dn = dxy || (gf.dir[4] && k == 0) || (gf.dir[5] && k == gf.nz - 1);
+    if (dn) {
+      ef[idx] = base ? base[idx] : from_acc<T>(A(0));
+      continue;
+    }
+    ef[idx] = from_acc<T>(base ? v0 + to_acc(base[idx]) : v0);
+  }
+}
+
 template <typename T>
 int restrict_t(const void* rf, const LevelGeom& gf, void* rc, const LevelGeom& gc, cudaStream_t s) {
   dim3 blk(32, 4);
@@ -140,6 +240,35 @@ int launch_prolong_base(nn4_dtype dt, const void* ec, const LevelGeom& gc, void*
 int launch_prolong(nn4_dtype dt, const void* ec, const LevelGeom& gc, void* ef,
                    const LevelGeom& gf, int accumulate, cudaStream_t s) {
   return launch_prolong_base(dt, ec, gc, ef, accumulate ? ef : nullptr, gf, s);
+}
+
+int batch_xfer_blocks(BatchXfer* X, bool prolong) {
+  const LevelGeom& g = prolong ? X->gf : X->gc;
+  X->bx = (g.nx + 31) / 32;
+  X->by = (g.ny + 3) / 4;
+  const int bz = prolong ? (g.nz + kPz - 1) / kPz : g.nz;
+  return X->bx * X->by * bz;
+}
+
+int launch_xfer_batch(nn4_dtype dt, bool prolong, const BatchXfer* tab, int count, int total, const int* active,
+                      cudaStream_t s) {
+  if (total <= 0) return NN4_OK;
+  dim3 blk(32, 4);
+  switch (dt) {
+    case NN4_F64:
+      if (prolong) k_prolong_batch<double><<<total, blk, 0, s>>>(tab, count, total, active);
+      else k_restrict_batch<double><<<total, blk, 0, s>>>(tab, count, total, active);
+      break;
+    case NN4_F32:
+      if (prolong) k_prolong_batch<float><<<total, blk, 0, s>>>(tab, count, total, active);
+      else k_restrict_batch<float><<<total, blk, 0, s>>>(tab, count, total, active);
+      break;
+    case NN4_BF16:
+      if (prolong) k_prolong_batch<bf16><<<total, blk, 0, s>>>(tab, count, total, active);
+      else k_restrict_batch<bf16><<<total, blk, 0, s>>>(tab, count, total, active);
+      break;
+  }
+  return check_cuda(cudaGetLastError(), "batched transfer launch");
 }
 
 }  // namespace nn4
