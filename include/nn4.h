@@ -198,6 +198,32 @@ typedef struct {
 
 int nn4_plan_query(nn4_plan p, nn4_plan_info* out);
 
+/* ----------------------------------------------------------------- batched solves */
+
+typedef struct nn4_batch_s* nn4_batch;
+
+/* A batch of `count` independent constant-coefficient pressure systems on grids of uneven sizes
+ * (grids[i]: node counts, spacing (equal on the three axes), faces, and the pitch of that
+ * instance's FP64 arrays).  Options as for nn4_plan_create: `inner` storage type and
+ * `inner_cycles` V-cycles per outer FP64 defect-correction iteration (Section 2.4's repeated
+ * cycles); `check_every` sets how often the host reads the per-instance convergence flags.  Every
+ * step of the cycle is one launch over the work items of all instances (the batching form; not
+ * in the paper).  Allocates all workspace here.  Errors: NN4_EINVAL, NN4_EUNSUPPORTED (unequal
+ * spacings, fewer than two levels, coarsest level above 1024 free nodes), NN4_ENOMEM. */
+int nn4_batch_create(const nn4_grid* grids, int32_t count, const nn4_plan_opts* opts, nn4_batch* out);
+
+int nn4_batch_destroy(nn4_batch b);
+
+/* Solves every instance from its x (bs[i], xs[i]: host arrays of device pointers to FP64 arrays)
+ * until its own relative residual <= rtol or max_iters outer iterations; converged instances stop
+ * early (their work items are skipped).  infos (host, count entries, nullable) receives each
+ * instance's iterations and final relative residual; latency_ms (host, nullable) the time from the
+ * start of the solve to the instance's convergence, from device %globaltimer stamps (-1 if it did
+ * not converge).  Synchronises the stream.  Returns NN4_ENOCONV if any instance hit the cap,
+ * NN4_ENONFINITE if any residual was not finite. */
+int nn4_pressure_solve_batched(nn4_batch b, const double* const* bs, double* const* xs, double rtol,
+                               int32_t max_iters, nn4_solve_info* infos, float* latency_ms, void* stream);
+
 /* ----------------------------------------------------------------- explicit multiphase terms */
 
 /* Constants of the compressive Petrov-Galerkin volume-fraction scheme (Sections 2.3.5-2.3.6). */
@@ -254,6 +280,79 @@ int nn4_vof_advect_residual_static(const nn4_grid* g, const nn4_vof_params* p, c
 /* *out (device FP64) = sum_i m_i C_i with m the lumped nodal volume: the C(t) of the mass
  * diagnostic (Section 3, mass conservation), accumulated in FP64. */
 int nn4_mass_sum(const nn4_grid* g, const double* C, double* out, void* stream);
+
+/* Physical constants and scheme settings of a multiphase run (Sections 2.1-2.4). */
+typedef struct {
+  double dt;                 /* time step */
+  double rho_l, rho_g;       /* densities of liquid (C = 1) and gas */
+  double mu_l, mu_g;         /* viscosities; mu = mu_l C + mu_g (1 - C) */
+  double sigma_t;            /* surface tension coefficient */
+  double g;                  /* gravity magnitude, acting along -z */
+  double alpha_a;            /* Eq. a_psi: 2 */
+  double eps_k;              /* Eqs. k-abs, h_Psi, k-square: 1e-7 */
+  int32_t p;                 /* polynomial order (1) */
+  int32_t momentum_iters;    /* Stage 2 predictor iterations (2) */
+  int32_t correction_iters;  /* Stage 3 pressure-velocity corrections N_I (2) */
+  int32_t pressure_cycles;   /* outer iterations per pressure solve when pressure_rtol <= 0 (20) */
+  double pressure_rtol;      /* > 0: solve each pressure equation to this relative residual */
+} nn4_flow_params;
+
+void nn4_flow_params_default(nn4_flow_params* p, double dt);
+
+/* Momentum sources (Eqs. surface-tension-uvw, surface-tension-k, gravity): s_d = sigma_t kappa
+ * C_d, and s_z -= g rho, with C_d the pointwise gradient m^-1 f(C; w_d), normals C_d / (eps_t +
+ * |grad C|), eps_t = 1e-7 / min(h), kappa = m^-1 sum_d f(n_d; w_d).  s0, s1, s2: outputs; kappa:
+ * optional output; workspace: 3 FP64 fields (3 * pitch * ny * nz doubles).  FP64 device arrays on g. */
+int nn4_momentum_sources(const nn4_grid* g, const nn4_flow_params* fp, const double* C, double* s0, double* s1,
+                         double* s2, double* kappa, double* workspace, void* stream);
+
+/* Stage-1 right-hand side (Eq. ph_disc, continuum signs): b = sum_d G_d^T s_d, G_d the assembled
+ * first-derivative filter w_d, 0 on the Dirichlet faces of g (the pressure faces). */
+int nn4_pressure_rhs_hs(const nn4_grid* g, const double* s0, const double* s1, const double* s2, double* b,
+                        void* stream);
+
+/* Stage-3 right-hand side (Eq. ph_disc2): b = -(1/dt) sum_d [ f(rho u~_d; w_d) - u~_d f(rho; w_d) ],
+ * rho from C; 0 on the Dirichlet faces of g.  rho_ws: one FP64 field of workspace. */
+int nn4_pressure_rhs_nh(const nn4_grid* g, const nn4_flow_params* fp, const double* C, const double* u,
+                        const double* v, const double* w, double* b, double* rho_ws, void* stream);
+
+/* Eq. vel-cor and the Stage-3 updates: (u, v, w) += -dt m^-1 f(dp; w_d) / rho except on the
+ * Dirichlet (no-slip) faces of g, and p_nh += dp (p_nh may be NULL). */
+int nn4_velocity_correct(const nn4_grid* g, const nn4_flow_params* fp, const double* C, const double* dp, double* u,
+                         double* v, double* w, double* p_nh, void* stream);
+
+/* One Stage-2 predictor iteration for the three components (Eqs. Petrov-u/v/w, k_Psi-n, k-abs,
+ * k-square, max-k, velocity-1 with sigma = 0): from u^n (un), the current u^{n+1/2} (uh, updated in
+ * place to (u^n + u~)/2), the total pressure p = p_hs + p_nh and the sources s (from
+ * nn4_momentum_sources), writes u~ (ut).  un, uh, ut, s: arrays of three device pointers.
+ * Dirichlet faces of g are no-slip walls.  workspace: 5 FP64 fields. */
+int nn4_momentum_predict(const nn4_grid* g, const nn4_flow_params* fp, const double* C, const double* const* un,
+                         double* const* uh, double* const* ut, const double* p, const double* const* s,
+                         double* workspace, void* stream);
+
+/* A multiphase time stepper: Stage 1 (hydrostatic + surface-tension pressure), Stage 2 (momentum
+ * predictor), Stage 3 (N_I non-hydrostatic pressure corrections), Stage 4 (volume fraction) of
+ * Section 2.4, with the pressure solves of a plan created with popts.  vel_grid: the node grid
+ * with the no-slip faces as Dirichlet; p_grid: the same nodes with the pressure faces (Dirichlet
+ * where p = 0).  All workspace is allocated here. */
+typedef struct nn4_flow_s* nn4_flow;
+
+typedef struct {
+  double mass;          /* sum_i m_i C_i after the step */
+  double c_min, c_max;  /* range of C after the step */
+  int32_t hs_iters;     /* outer iterations of the Stage-1 solve */
+  int32_t nh_iters;     /* outer iterations of the last Stage-3 solve */
+  double hs_rel, nh_rel;
+} nn4_flow_stats;
+
+int nn4_flow_create(const nn4_grid* vel_grid, const nn4_grid* p_grid, const nn4_flow_params* fp,
+                    const nn4_plan_opts* popts, nn4_flow* out);
+int nn4_flow_destroy(nn4_flow f);
+
+/* Advances the caller's device state (FP64, vel_grid pitch) by one step in place: C, u, v, w at
+ * level n -> n+1, p_hs and p_nh updated.  stats: host, nullable.  Synchronises the stream. */
+int nn4_flow_step(nn4_flow f, double* C, double* u, double* v, double* w, double* p_hs, double* p_nh,
+                  nn4_flow_stats* stats, void* stream);
 
 /* ----------------------------------------------------------------- diagnostics */
 

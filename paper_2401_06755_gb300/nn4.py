@@ -57,6 +57,19 @@ class _VOFParams(ctypes.Structure):
                [("p", ctypes.c_int32)]
 
 
+class _FlowParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("dt", "rho_l", "rho_g", "mu_l", "mu_g", "sigma_t", "g", "alpha_a",
+                                               "eps_k")] + \
+               [("p", ctypes.c_int32), ("momentum_iters", ctypes.c_int32), ("correction_iters", ctypes.c_int32),
+                ("pressure_cycles", ctypes.c_int32), ("pressure_rtol", ctypes.c_double)]
+
+
+class _FlowStats(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("c_min", ctypes.c_double), ("c_max", ctypes.c_double),
+                ("hs_iters", ctypes.c_int32), ("nh_iters", ctypes.c_int32), ("hs_rel", ctypes.c_double),
+                ("nh_rel", ctypes.c_double)]
+
+
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -98,6 +111,24 @@ def lib():
             "nn4_vof_workspace_bytes": (ctypes.c_int64, [G]),
             "nn4_vof_advect_residual": (ctypes.c_int, [G, ctypes.POINTER(_VOFParams), vp, vp, vp, vp, vp, vp, vp, vp]),
             "nn4_mass_sum": (ctypes.c_int, [G, vp, vp, vp]),
+            "nn4_batch_create": (ctypes.c_int, [G, i32, ctypes.POINTER(_PlanOpts), ctypes.POINTER(vp)]),
+            "nn4_batch_destroy": (ctypes.c_int, [vp]),
+            "nn4_pressure_solve_batched": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dbl, i32,
+                                                          ctypes.POINTER(_SolveInfo), ctypes.POINTER(ctypes.c_float),
+                                                          vp]),
+            "nn4_vof_advect_residual_static": (ctypes.c_int, [G, ctypes.POINTER(_VOFParams), vp, vp, vp, vp, vp, vp, vp]),
+            "nn4_flow_params_default": (None, [ctypes.POINTER(_FlowParams), dbl]),
+            "nn4_momentum_sources": (ctypes.c_int, [G, ctypes.POINTER(_FlowParams), vp, vp, vp, vp, vp, vp, vp]),
+            "nn4_pressure_rhs_hs": (ctypes.c_int, [G, vp, vp, vp, vp, vp]),
+            "nn4_pressure_rhs_nh": (ctypes.c_int, [G, ctypes.POINTER(_FlowParams), vp, vp, vp, vp, vp, vp, vp]),
+            "nn4_velocity_correct": (ctypes.c_int, [G, ctypes.POINTER(_FlowParams), vp, vp, vp, vp, vp, vp, vp]),
+            "nn4_momentum_predict": (ctypes.c_int, [G, ctypes.POINTER(_FlowParams), vp, ctypes.POINTER(vp),
+                                                    ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.POINTER(vp),
+                                                    vp, vp]),
+            "nn4_flow_create": (ctypes.c_int, [G, G, ctypes.POINTER(_FlowParams), ctypes.POINTER(_PlanOpts),
+                                               ctypes.POINTER(vp)]),
+            "nn4_flow_destroy": (ctypes.c_int, [vp]),
+            "nn4_flow_step": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(_FlowStats), vp]),
             "nn4_last_error": (ctypes.c_char_p, []),
             "nn4_device_error": (ctypes.c_int, []),
             "nn4_version": (ctypes.c_char_p, []),
@@ -326,3 +357,130 @@ class Plan:
         assert b.device.type == "cpu" and x.device.type == "cpu" and b.is_contiguous() and x.is_contiguous()
         return self._solve(lib().nn4_pressure_solve_host, b, x, rtol, max_iters, history_len, stream,
                            lambda t: ctypes.c_void_p(t.data_ptr()))
+
+
+class Batch:
+    """Many independent constant-coefficient pressure systems of uneven sizes, solved together."""
+
+    def __init__(self, grids, inner=F32, inner_cycles=2, omega=2.0 / 3.0, check_every=1):
+        o = _PlanOpts()
+        lib().nn4_plan_opts_default(ctypes.byref(o))
+        o.inner, o.inner_cycles, o.omega, o.check_every = int(inner), int(inner_cycles), float(omega), int(check_every)
+        self.grids = list(grids)
+        arr = (_Grid * len(self.grids))(*[g.c(torch.float64) for g in self.grids])
+        h = ctypes.c_void_p(0)
+        _check(lib().nn4_batch_create(arr, len(self.grids), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().nn4_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, bs, xs, rtol=1e-8, max_iters=100, stream=None):
+        """bs, xs: lists of FP64 storage tensors.  Returns (status, infos, latency_ms)."""
+        n = len(self.grids)
+        bp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in bs])
+        xp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in xs])
+        infos = (_SolveInfo * n)()
+        lat = (ctypes.c_float * n)()
+        code = lib().nn4_pressure_solve_batched(self._h, bp, xp, float(rtol), int(max_iters), infos, lat,
+                                                _stream(stream))
+        if code not in (OK, ENOCONV):
+            _check(code)
+        return code, [{"iterations": infos[i].iterations, "rel_res": infos[i].rel_res,
+                       "kernels": infos[i].kernels} for i in range(n)], list(lat)
+
+
+def flow_params(dt, **over):
+    p = _FlowParams()
+    lib().nn4_flow_params_default(ctypes.byref(p), float(dt))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def _arr3(ts):
+    return (ctypes.c_void_p * 3)(*[t.data_ptr() for t in ts])
+
+
+def momentum_sources(grid, fp, C, stream=None):
+    s = [torch.empty_like(C) for _ in range(3)]
+    kappa = torch.empty_like(C)
+    ws = torch.empty((3,) + tuple(C.shape), dtype=torch.float64, device=C.device)
+    g = grid.c(torch.float64)
+    _check(lib().nn4_momentum_sources(ctypes.byref(g), ctypes.byref(fp), _ptr(C), _ptr(s[0]), _ptr(s[1]),
+                                      _ptr(s[2]), _ptr(kappa), _ptr(ws), _stream(stream)))
+    return s, kappa
+
+
+def pressure_rhs_hs(pgrid, s, stream=None):
+    b = torch.empty_like(s[0])
+    g = pgrid.c(torch.float64)
+    _check(lib().nn4_pressure_rhs_hs(ctypes.byref(g), _ptr(s[0]), _ptr(s[1]), _ptr(s[2]), _ptr(b), _stream(stream)))
+    return b
+
+
+def pressure_rhs_nh(pgrid, fp, C, ut, stream=None):
+    b = torch.empty_like(C)
+    rho = torch.empty_like(C)
+    g = pgrid.c(torch.float64)
+    _check(lib().nn4_pressure_rhs_nh(ctypes.byref(g), ctypes.byref(fp), _ptr(C), _ptr(ut[0]), _ptr(ut[1]),
+                                     _ptr(ut[2]), _ptr(b), _ptr(rho), _stream(stream)))
+    return b
+
+
+def velocity_correct(vgrid, fp, C, dp, u, p_nh=None, stream=None):
+    g = vgrid.c(torch.float64)
+    _check(lib().nn4_velocity_correct(ctypes.byref(g), ctypes.byref(fp), _ptr(C), _ptr(dp), _ptr(u[0]), _ptr(u[1]),
+                                      _ptr(u[2]), _ptr(p_nh), _stream(stream)))
+    return u
+
+
+def momentum_predict(vgrid, fp, C, un, uh, p, s, stream=None):
+    """One predictor iteration; uh is updated in place; returns u~."""
+    ut = [torch.empty_like(C) for _ in range(3)]
+    ws = torch.empty((5,) + tuple(C.shape), dtype=torch.float64, device=C.device)
+    g = vgrid.c(torch.float64)
+    _check(lib().nn4_momentum_predict(ctypes.byref(g), ctypes.byref(fp), _ptr(C), _arr3(un), _arr3(uh), _arr3(ut),
+                                      _ptr(p), _arr3(s), _ptr(ws), _stream(stream)))
+    return ut
+
+
+class Flow:
+    """The four-stage multiphase time step on device state (Section 2.4)."""
+
+    def __init__(self, vgrid, pgrid, fp, inner=F64, inner_cycles=1, outer=OUTER_CYCLES):
+        o = _PlanOpts()
+        lib().nn4_plan_opts_default(ctypes.byref(o))
+        o.inner, o.inner_cycles, o.outer = int(inner), int(inner_cycles), int(outer)
+        self._gv, self._gp = vgrid.c(torch.float64), pgrid.c(torch.float64)
+        self.fp = fp
+        h = ctypes.c_void_p(0)
+        _check(lib().nn4_flow_create(ctypes.byref(self._gv), ctypes.byref(self._gp), ctypes.byref(fp),
+                                     ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def step(self, C, u, v, w, p_hs, p_nh, stream=None):
+        st = _FlowStats()
+        _check(lib().nn4_flow_step(self._h, _ptr(C), _ptr(u), _ptr(v), _ptr(w), _ptr(p_hs), _ptr(p_nh),
+                                   ctypes.byref(st), _stream(stream)))
+        return {"mass": st.mass, "c_min": st.c_min, "c_max": st.c_max, "hs_iters": st.hs_iters,
+                "nh_iters": st.nh_iters, "hs_rel": st.hs_rel, "nh_rel": st.nh_rel}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().nn4_flow_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -83,3 +83,15 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", text, flags=re.M), f
                 assert "oracle/" not in text, f
+
+
+def test_no_unresolved_internal_symbols(nn4):
+    """Every internal (nn4 namespace) symbol the library references is defined in it."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if not nm:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "--undefined-only", nn4.LIB_PATH], capture_output=True, text=True).stdout
+    bad = [l for l in out.splitlines() if "_ZN3nn4" in l]
+    assert not bad, bad
