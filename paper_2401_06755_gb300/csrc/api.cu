@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -28,6 +29,37 @@ int check_cuda(cudaError_t e, const char* what) {
 }
 
 size_t dtype_size(nn4_dtype dt) { return dt == NN4_F64 ? 8 : (dt == NN4_F32 ? 4 : 2); }
+
+int sm_count() {
+  static std::mutex mu;
+  static int counts[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  std::lock_guard<std::mutex> lock(mu);
+  if (counts[dev] == 0) {
+    int n = 0;
+    counts[dev] = (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0) ? n : 152;
+  }
+  return counts[dev];
+}
+
+long long resident_grid(const void* kern, int threads, size_t smem, long long want) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void*, int>, int>> cache;  // (kernel, threads) -> blocks/SM
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& e : cache)
+      if (e.first.first == kern && e.first.second == threads) per_sm = e.second;
+    if (per_sm == 0) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+      cache.push_back({{kern, threads}, per_sm});
+    }
+  }
+  const long long cap = (long long)per_sm * sm_count();
+  return want < 1 ? 1 : (want < cap ? want : cap);
+}
 
 Coef8 stencil_coef(const double h[3]) {
   // Interior Q1 stiffness = K(x)M(y)M(z) + M(x)K(y)M(z) + M(x)M(y)K(z) with the 1D stencils
@@ -139,7 +171,7 @@ const char* nn4_version(void) { return "nn4-gb300 0.1 (sm_103a)"; }
 int nn4_device_error(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return check_cuda(e, "device synchronise");
-  const unsigned int w = stencil_error_word() | flow_error_word();
+  const unsigned int w = stencil_error_word() | flow_error_word() | tail_error_word();
   if (w & 1u) return set_error(NN4_ETIMEOUT, "a bounded device wait gave up");
   if (w & 2u) return set_error(NN4_EBOUNDS, "a checked device index was out of range");
   return NN4_OK;

@@ -33,6 +33,19 @@ template <> __device__ __forceinline__ float from_acc<float>(float v) { return v
 template <> __device__ __forceinline__ bf16 from_acc<bf16>(float v) { return __float2bfloat16_rn(v); }
 template <> __device__ __forceinline__ double from_acc<double>(float v) { return (double)v; }
 
+// A value the compiler treats as opaque: a loop-invariant conversion (e.g. of an FP64 kernel
+// argument) is then computed once and kept, not recomputed at each use.
+__device__ __forceinline__ float opaque(float v) {
+  float r;
+  asm volatile("mov.b32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ double opaque(double v) {
+  double r;
+  asm volatile("mov.b64 %0, %1;" : "=d"(r) : "d"(v));
+  return r;
+}
+
 // ---------------------------------------------------------------- device error word
 // Bit 0: a bounded wait gave up.  Bit 1: a checked index was out of range.  Each translation
 // unit has its own word (no relocatable device code); NN4_DEFINE_ERROR_ACCESSOR(name) gives the

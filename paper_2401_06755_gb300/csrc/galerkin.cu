@@ -150,13 +150,19 @@ __global__ void k_pass27(const T* __restrict__ x, const T* __restrict__ a27, con
   if (i >= g.nx || j >= g.ny) return;
   const long long plane = g.pitch * (long long)g.ny * g.nz;
   const long long o = i + g.pitch * ((long long)j + (long long)g.ny * k);
+  // the three mirrored x indices and nine row offsets once per node; coefficient d sits d planes
+  // (of the 27-array block) after coefficient 0
+  const int ix[3] = {mirror(i - 1, g.nx), i, mirror(i + 1, g.nx)};
+  long long row[9];
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+      row[dy + 3 * dz] = g.pitch * ((long long)mirror(j + dy - 1, g.ny) + (long long)g.ny * mirror(k + dz - 1, g.nz));
+  const T* ap = a27 + o;
   A s = 0;
 #pragma unroll
-  for (int d = 0; d < 27; ++d) {
-    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-    const int i2 = mirror(i + dx, g.nx), j2 = mirror(j + dy, g.ny), k2 = mirror(k + dz, g.nz);
-    s += to_acc(a27[d * plane + o]) * to_acc(x[i2 + g.pitch * ((long long)j2 + (long long)g.ny * k2)]);
-  }
+  for (int d = 0; d < 27; ++d) s += to_acc(ap[d * plane]) * to_acc(x[row[d / 3] + ix[d % 3]]);
   const bool dn = dnode(g, i, j, k);
   const A bv = to_acc(reinterpret_cast<const T*>(a.b)[o]);
   T* out = reinterpret_cast<T*>(a.out);
@@ -164,8 +170,14 @@ __global__ void k_pass27(const T* __restrict__ x, const T* __restrict__ a27, con
     out[o] = from_acc<T>(dn ? A(0) : bv - s);
   } else {
     const A xc = to_acc(x[o]);
-    const A D = to_acc(a27[13 * plane + o]);
-    out[o] = from_acc<T>(dn ? xc : xc + (A)a.omega * (bv - s) / D);
+    const A D = to_acc(ap[13 * plane]);
+    const A omega = (A)a.omega;
+    A corr;
+    if constexpr (sizeof(A) == 4)
+      corr = __fdividef(bv - s, D);
+    else
+      corr = (bv - s) / D;
+    out[o] = from_acc<T>(dn ? xc : xc + omega * corr);
   }
 }
 

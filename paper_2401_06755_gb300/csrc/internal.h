@@ -61,10 +61,16 @@ int check_cuda(cudaError_t e, const char* what);
 bool make_tmap_3d(CUtensorMap* map, nn4_dtype dt, const void* base, int nx, int ny, int nz,
                   long long pitch, int box_x, int box_y);
 size_t dtype_size(nn4_dtype dt);
+// SMs of the current device (cached per device).
+int sm_count();
+// min(want, the blocks of `kern` that are resident at once with `threads` threads and `smem`
+// dynamic shared memory): the grid of a grid-stride kernel, so no block waits for a second wave.
+long long resident_grid(const void* kern, int threads, size_t smem, long long want);
 
 // Per-unit device error words (read and cleared).
 unsigned int stencil_error_word();
 unsigned int flow_error_word();
+unsigned int tail_error_word();
 
 // ---------------------------------------------------------------- launchers
 // Tensor maps of one stencil pass: haloed tiles of x and k, pointwise tiles of b, L k, 1/diag.
@@ -118,7 +124,7 @@ int launch_coarse_solve(nn4_dtype dt, const double* ainv, const int* free_idx, i
 // tail.cu: the coarse levels of a V-cycle in one single-CTA launch.  Level 0 of the tail is the
 // entry level (its r holds the restricted residual on entry, its e the correction on exit);
 // the last level is the coarsest (dense solve with ainv over free_idx).
-constexpr int kMaxTail = 8;
+constexpr int kMaxTail = 12;
 constexpr int kTailNodes = 800;  // levels at or below this many nodes join the tail (9^3)
 
 struct TailLevel {
@@ -132,6 +138,7 @@ struct TailLevel {
 
 struct TailArgs {
   int nlev;
+  int dense_all;  // the last level is solved by ainv over all its nodes (free_idx: every node)
   TailLevel lv[kMaxTail];
   const double* ainv;
   const int* free_idx;
@@ -140,6 +147,19 @@ struct TailArgs {
 };
 
 int launch_tail(nn4_dtype dt, const TailArgs& a, cudaStream_t s);
+
+// Cooperative launch over all SMs for levels lv[0 .. nlev-1] (the first with at most
+// kCoarseNodes nodes down to the level solved by the dense map in ainv, dense_all = 1): the
+// restrictions, the dense map, then a fused prolongation + Jacobi sweep per level back up, with
+// grid barriers between the steps (`bar`: a zeroed GridBarrier in device memory owned by the
+// caller).
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+};
+constexpr int kCoarseThreads = 512;
+constexpr long long kCoarseNodes = 300000;
+int launch_coarse(nn4_dtype dt, const TailArgs& a, GridBarrier* bar, cudaStream_t s);
 // One CTA per instance (tab: device array of `count` tails; `active` skips converged ones).
 int launch_tail_batch(nn4_dtype dt, const TailArgs* tab, int count, const int* active, cudaStream_t s);
 

@@ -74,7 +74,23 @@ struct PlanImpl {
   double* hist = nullptr;
   int hist_cap = 0;
   double* host_hist = nullptr;  // pinned
-  int tail_start = -1;  // first level handled by the single-launch coarse tail (-1: none)
+  // Coarse levels in one launch: levels >= tail_start run in the single-CTA tail or, with
+  // coarse_coop, in the cooperative kernel; coarse_top (>= 1, or -1) is the level above them whose
+  // restriction and prolongation the cooperative kernel also performs.
+  int tail_start = -1;
+  bool coarse_coop = false;
+  int coarse_top = -1;
+  GridBarrier* gbar = nullptr;
+  // cooperative form: levels tail_start .. coarse_dense run in the kernel, and everything at and
+  // below coarse_dense is applied as one dense FP64 map (tail_map, n x n over all its nodes at the
+  // offsets tail_idx)
+  int coarse_dense = -1;
+  double* tail_map = nullptr;
+  int* tail_idx = nullptr;
+  int tail_n = 0;
+  // host copies of the coarsest inverse (for the dense map)
+  std::vector<double> ainv_host;
+  std::vector<int> free_lin_host;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int64_t graph_kernels[2] = {0, 0};
   cudaStream_t graph_stream = nullptr;
@@ -292,6 +308,8 @@ int build_coarsest(PlanImpl* P, const std::vector<double>& dense_all) {
   if (!invert(A, n)) return set_error(NN4_EINVAL, "coarsest operator is singular");
   if (singular)
     for (auto& v : A) v -= 1.0 / n;
+  P->ainv_host = A;
+  P->free_lin_host = free_lin;
   int rc;
   if ((rc = alloc(P, (void**)&P->ainv, sizeof(double) * n * n))) return rc;
   if ((rc = alloc(P, (void**)&P->free_idx, sizeof(int) * n))) return rc;
@@ -300,6 +318,163 @@ int build_coarsest(PlanImpl* P, const std::vector<double>& dense_all) {
   if ((rc = check_cuda(cudaMemcpy(P->free_idx, free_off.data(), sizeof(int) * n, cudaMemcpyHostToDevice), "copy idx")))
     return rc;
   P->nfree = n;
+  return NN4_OK;
+}
+
+// ---------------------------------------------------------------- dense tail map
+// With a zero initial guess, everything the cycle does at and below level T (restriction to the
+// coarsest level, the coarsest solve, prolongation and one Jacobi sweep per level back up to T)
+// is a linear map r_T -> e_T.  The cooperative form applies it as one dense mat-vec; it is built
+// here column by column by running exactly those steps on the host in FP64 on unit vectors, with
+// the coefficients the device holds (converted exactly to FP64).
+struct HostLevel {
+  LevelGeom g;
+  Coef8 L;
+  std::vector<double> a27;  // [27][nodes], empty for the constant operator
+  int n = 0;
+};
+
+int host_level(PlanImpl* P, int l, HostLevel* H) {
+  const Level& L = P->lv[l];
+  H->g = L.g;
+  H->L = L.L;
+  H->n = L.g.nx * L.g.ny * L.g.nz;
+  if (!(P->vc && L.a27)) return NN4_OK;
+  const size_t plane = (size_t)L.g.pitch * L.g.ny * L.g.nz, es = dtype_size(P->T);
+  std::vector<char> raw(kA27 * plane * es);
+  int rc;
+  if ((rc = check_cuda(cudaMemcpy(raw.data(), L.a27, raw.size(), cudaMemcpyDeviceToHost), "copy tail coefficients")))
+    return rc;
+  H->a27.assign((size_t)kA27 * H->n, 0.0);
+  for (int d = 0; d < kA27; ++d)
+    for (int k = 0; k < L.g.nz; ++k)
+      for (int j = 0; j < L.g.ny; ++j)
+        for (int i = 0; i < L.g.nx; ++i) {
+          const size_t o = d * plane + i + L.g.pitch * (j + (size_t)L.g.ny * k);
+          double v;
+          if (P->T == NN4_F64) {
+            v = reinterpret_cast<const double*>(raw.data())[o];
+          } else if (P->T == NN4_F32) {
+            v = reinterpret_cast<const float*>(raw.data())[o];
+          } else {
+            uint16_t h;
+            std::memcpy(&h, raw.data() + o * 2, 2);
+            const uint32_t w = (uint32_t)h << 16;
+            float f;
+            std::memcpy(&f, &w, 4);
+            v = f;
+          }
+          H->a27[(size_t)d * H->n + i + L.g.nx * (j + (size_t)L.g.ny * k)] = v;
+        }
+  return NN4_OK;
+}
+
+int hmirror(int i, int n) { return i < 0 ? -i : (i >= n ? 2 * (n - 1) - i : i); }
+
+void host_restrict(const HostLevel& F, const HostLevel& C, const std::vector<double>& rf, std::vector<double>& rc) {
+  const LevelGeom &f = F.g, &c = C.g;
+  rc.assign(C.n, 0.0);
+  for (int K = 0; K < c.nz; ++K)
+    for (int J = 0; J < c.ny; ++J)
+      for (int I = 0; I < c.nx; ++I) {
+        if (is_dir(c, I, J, K)) continue;
+        double acc = 0.0;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+              if (i < 0 || i >= f.nx || j < 0 || j >= f.ny || k < 0 || k >= f.nz) continue;
+              acc += (dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0) * rf[i + f.nx * (j + f.ny * k)];
+            }
+        rc[I + c.nx * (J + c.ny * K)] = acc;
+      }
+}
+
+void host_prolong(const HostLevel& C, const HostLevel& F, const std::vector<double>& ec, std::vector<double>& t) {
+  const LevelGeom &f = F.g, &c = C.g;
+  t.assign(F.n, 0.0);
+  for (int k = 0; k < f.nz; ++k)
+    for (int j = 0; j < f.ny; ++j)
+      for (int i = 0; i < f.nx; ++i) {
+        if (is_dir(f, i, j, k)) continue;
+        double v = 0.0;
+        for (int cz = 0; cz < 2; ++cz)
+          for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx)
+              v += ec[((i >> 1) + cx * (i & 1)) + c.nx * (((j >> 1) + cy * (j & 1)) + c.ny * ((k >> 1) + cz * (k & 1)))];
+        t[i + f.nx * (j + f.ny * k)] = 0.125 * v;
+      }
+}
+
+void host_jacobi(const HostLevel& L, double omega, const std::vector<double>& t, const std::vector<double>& r,
+                 std::vector<double>& e) {
+  const LevelGeom& g = L.g;
+  e.assign(L.n, 0.0);
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        const int o = i + g.nx * (j + g.ny * k);
+        if (is_dir(g, i, j, k)) {
+          e[o] = t[o];
+          continue;
+        }
+        double s = 0.0, D;
+        for (int d = 0; d < kA27; ++d) {
+          const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+          const double xv = t[hmirror(i + dx, g.nx) + g.nx * (hmirror(j + dy, g.ny) + g.ny * hmirror(k + dz, g.nz))];
+          if (!L.a27.empty())
+            s += L.a27[(size_t)d * L.n + o] * xv;
+          else
+            s += L.L.c[(dx != 0) + 2 * (dy != 0) + 4 * (dz != 0)] * xv;
+        }
+        if (!L.a27.empty()) {
+          D = L.a27[(size_t)13 * L.n + o];
+        } else {
+          const double w = 0.125 * ((i > 0) + (i < g.nx - 1)) * ((j > 0) + (j < g.ny - 1)) * ((k > 0) + (k < g.nz - 1));
+          s *= w;
+          D = w * L.L.c[0];
+        }
+        e[o] = t[o] + omega * (r[o] - s) / D;
+      }
+}
+
+int build_tail_map(PlanImpl* P) {
+  const int nl = (int)P->lv.size(), T = P->coarse_dense;
+  std::vector<HostLevel> H(nl);
+  int rc;
+  for (int l = T; l < nl; ++l)
+    if ((rc = host_level(P, l, &H[l]))) return rc;
+  const int n = H[T].n, nf = P->nfree;
+  std::vector<double> M((size_t)n * n, 0.0);
+  std::vector<std::vector<double>> r(nl), e(nl);
+  std::vector<double> t;
+  for (int c = 0; c < n; ++c) {
+    r[T].assign(n, 0.0);
+    r[T][c] = 1.0;
+    for (int l = T; l + 1 < nl; ++l) host_restrict(H[l], H[l + 1], r[l], r[l + 1]);
+    e[nl - 1].assign(H[nl - 1].n, 0.0);
+    for (int a = 0; a < nf; ++a) {
+      double v = 0.0;
+      for (int b = 0; b < nf; ++b) v += P->ainv_host[(size_t)a * nf + b] * r[nl - 1][P->free_lin_host[b]];
+      e[nl - 1][P->free_lin_host[a]] = v;
+    }
+    for (int l = nl - 2; l >= T; --l) {
+      host_prolong(H[l + 1], H[l], e[l + 1], t);
+      host_jacobi(H[l], P->o.omega, t, r[l], e[l]);
+    }
+    for (int a = 0; a < n; ++a) M[(size_t)a * n + c] = e[T][a];
+  }
+  std::vector<int> idx(n);
+  const LevelGeom& g = P->lv[T].g;
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) idx[i + g.nx * (j + g.ny * k)] = (int)(i + g.pitch * (j + (long long)g.ny * k));
+  if ((rc = alloc(P, (void**)&P->tail_map, sizeof(double) * M.size())) ||
+      (rc = alloc(P, (void**)&P->tail_idx, sizeof(int) * n)) ||
+      (rc = check_cuda(cudaMemcpy(P->tail_map, M.data(), sizeof(double) * M.size(), cudaMemcpyHostToDevice), "copy tail map")) ||
+      (rc = check_cuda(cudaMemcpy(P->tail_idx, idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice), "copy tail index")))
+    return rc;
+  P->tail_n = n;
   return NN4_OK;
 }
 
@@ -364,17 +539,21 @@ int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
   }
   if ((rc = K(P, "restrict:L0", s, [&] { return launch_restrict(T, r0, L0.g, P->lv[1].r, P->lv[1].g, s); })))
     return rc;
-  const int ts = P->tail_start > 0 ? P->tail_start : nl;  // levels >= ts run in the tail kernel
-  for (int l = 1; l + 1 < nl && l < ts; ++l)
+  const int ts = P->tail_start > 0 ? P->tail_start : nl;  // levels >= ts run in one launch
+  const int top = P->coarse_coop ? P->coarse_top : -1;     // its transfers run there too
+  const int host_down = top > 0 ? top : ts;                // host restrictions end at this level
+  for (int l = 1; l + 1 < nl && l < host_down; ++l)
     if ((rc = K(P, "restrict:" + lvl(l), s,
                 [&] { return launch_restrict(T, P->lv[l].r, P->lv[l].g, P->lv[l + 1].r, P->lv[l + 1].g, s); })))
       return rc;
   if (ts < nl) {
     TailArgs ta{};
-    ta.nlev = nl - ts;
-    for (int l = ts; l < nl; ++l) {
+    const int first = top > 0 ? top : ts;
+    const int last = P->coarse_coop ? P->coarse_dense : nl - 1;
+    ta.nlev = last - first + 1;
+    for (int l = first; l <= last; ++l) {
       Level& L = P->lv[l];
-      TailLevel& t = ta.lv[l - ts];
+      TailLevel& t = ta.lv[l - first];
       t.g = L.g;
       t.L = L.L;
       t.r = L.r;
@@ -382,11 +561,16 @@ int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
       t.t = L.t;
       t.a27 = P->vc ? L.a27 : nullptr;
     }
-    ta.ainv = P->ainv;
-    ta.free_idx = P->free_idx;
-    ta.nfree = P->nfree;
+    ta.ainv = P->coarse_coop ? P->tail_map : P->ainv;
+    ta.free_idx = P->coarse_coop ? P->tail_idx : P->free_idx;
+    ta.nfree = P->coarse_coop ? P->tail_n : P->nfree;
+    ta.dense_all = P->coarse_coop ? 1 : 0;
     ta.omega = P->o.omega;
-    if ((rc = K(P, "coarse_tail", s, [&] { return launch_tail(T, ta, s); }))) return rc;
+    if (P->coarse_coop) {
+      if ((rc = K(P, "coarse_levels", s, [&] { return launch_coarse(T, ta, P->gbar, s); }))) return rc;
+    } else if ((rc = K(P, "coarse_tail", s, [&] { return launch_tail(T, ta, s); }))) {
+      return rc;
+    }
   } else {
     Level& C = P->lv[nl - 1];
     if ((rc = K(P, "coarsest", s,
@@ -396,8 +580,9 @@ int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
   // up: prolongation then one Jacobi sweep per level above the tail
   for (int l = std::min(ts, nl - 1) - 1; l >= 1; --l) {
     Level& L = P->lv[l];
-    if ((rc = K(P, "prolong:" + lvl(l), s,
-                [&] { return launch_prolong_base(T, P->lv[l + 1].e, P->lv[l + 1].g, L.t, nullptr, L.g, s); })))
+    if (l != top && (rc = K(P, "prolong:" + lvl(l), s, [&] {
+                       return launch_prolong_base(T, P->lv[l + 1].e, P->lv[l + 1].g, L.t, nullptr, L.g, s);
+                     })))
       return rc;
     if ((rc = run_pass(P, l, OP_JACOBI, L.t, &L.m_jac, L.r, L.e, s))) return rc;
   }
@@ -775,9 +960,17 @@ int validate_plan_grid(const nn4_grid* g) {
   return NN4_OK;
 }
 
+// A grid barrier left half-counted by a wait that gave up (reported through the device error
+// word) is re-armed before the next solve or cycle.
+int reset_barrier(PlanImpl* P, cudaStream_t s) {
+  if (!P->gbar) return NN4_OK;
+  return check_cuda(cudaMemsetAsync(&P->gbar->count, 0, sizeof(unsigned), s), "reset grid barrier");
+}
+
 int solve_device(PlanImpl* P, double rtol, int32_t max_iters, nn4_solve_info* info, cudaStream_t s) {
   int rc;
   if (max_iters < 0) return set_error(NN4_EINVAL, "max_iters must be >= 0");
+  if ((rc = reset_barrier(P, s))) return rc;
   if (max_iters + 1 > P->hist_cap) {
     // grow the history buffers (outside any capture)
     const int cap = max_iters + 64;
@@ -947,14 +1140,33 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
   }
   {
     const int nl = (int)P->lv.size();
-    for (int l = 1; l < nl; ++l) {
-      const long long nodes = (long long)P->lv[l].g.nx * P->lv[l].g.ny * P->lv[l].g.nz;
-      if (nodes <= kTailNodes && nl - l <= kMaxTail) {
-        P->tail_start = l;
+    // entry: the first level below the finest with at most kCoarseNodes nodes.  At most
+    // kTailNodes nodes: the single-CTA tail; more: the cooperative kernel over all SMs.
+    auto nodes = [&](int l) { return (long long)P->lv[l].g.nx * P->lv[l].g.ny * P->lv[l].g.nz; };
+    int E = -1;
+    for (int l = 1; l < nl; ++l)
+      if (nodes(l) <= kCoarseNodes) {
+        E = l;
         break;
       }
+    if (o.coarse_tail && E > 0) {
+      if (nodes(E) <= kTailNodes) {
+        if (nl - E <= kMaxTail) P->tail_start = E;
+      } else {
+        // the dense map covers the first level with at most kTailNodes nodes (or the coarsest)
+        int T0 = nl - 1;
+        for (int l = E + 1; l < nl; ++l)
+          if (nodes(l) <= kTailNodes) {
+            T0 = l;
+            break;
+          }
+        if (T0 > E && nodes(T0) <= 1024 && T0 - E + 1 <= kMaxTail) {
+          P->tail_start = E;
+          P->coarse_coop = true;
+          P->coarse_dense = T0;
+        }
+      }
     }
-    if (!o.coarse_tail) P->tail_start = -1;
   }
   for (auto& L : P->lv) {
     L.L = stencil_coef(L.h);
@@ -965,6 +1177,10 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
       destroy(P);
       return rc;
     }
+  }
+  if (P->coarse_coop && (rc = alloc(P, (void**)&P->gbar, sizeof(GridBarrier)))) {
+    destroy(P);
+    return rc;
   }
   const size_t fb64 = field_bytes(P->g64, NN4_F64);
   if ((rc = alloc(P, (void**)&P->x64, fb64)) || (rc = alloc(P, (void**)&P->b64, fb64)) ||
@@ -1082,7 +1298,8 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
     }
     rc = NN4_OK;
   }
-  if (rc || (rc = build_coarsest(P, dense)) || (rc = check_cuda(cudaDeviceSynchronize(), "plan build"))) {
+  if (rc || (rc = build_coarsest(P, dense)) || (P->coarse_coop && (rc = build_tail_map(P))) ||
+      (rc = check_cuda(cudaDeviceSynchronize(), "plan build"))) {
     destroy(P);
     return rc;
   }
@@ -1105,6 +1322,8 @@ int nn4_vcycle(nn4_plan p, const void* b, void* x, void* stream) {
     return set_error(NN4_EINVAL, "arrays must be 16-byte aligned");
   PlanImpl* P = p->impl;
   Fine F{b, x, nullptr, nullptr};  // caller arrays: maps are built per launch
+  const int rc = reset_barrier(P, static_cast<cudaStream_t>(stream));
+  if (rc) return rc;
   return vcycle_impl(P, F, false, static_cast<cudaStream_t>(stream));
 }
 

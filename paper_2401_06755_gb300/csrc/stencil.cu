@@ -205,7 +205,10 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
     sk.zero();
   }
   A xc1[RY], kc1[RY];  // centre values of the previous input plane (the pending output)
-  double nrm = 0.0, dt2 = 0.0;
+  // norm and dot partial sums in the compute type for the whole z-march (FP32 for FP32 and BF16
+  // storage: the FP64 pipe of this part is narrow), FP64 across threads
+  A nrm = A(0), dt2 = A(0);
+  const A omega = opaque((A)a.omega);
   bool failed = false;
   T* out = reinterpret_cast<T*>(a.out);
 
@@ -230,6 +233,7 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
 
     const int kout = zs + q - 2;  // output plane completed by this input plane
     if (q >= 2 && !failed) {
+      A pn = A(0), pd = A(0);
       const A wz = (A)half_count(kout, nz);
       const bool dz = (g.dir[4] && kout == 0) || (g.dir[5] && kout == nz - 1);
 #pragma unroll
@@ -263,12 +267,12 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
             if (OP == OP_RESIDUAL) {
               const A rv = dirn ? A(0) : bv - Ax;
               out[idx] = from_acc<T>(rv);
-              nrm += (double)rv * (double)rv;
+              pn += rv * rv;
             } else if (OP == OP_MATVEC) {
               const A qv = dirn ? A(0) : Ax;
               out[idx] = from_acc<T>(qv);
-              nrm += (double)xc1[r] * (double)qv;
-              dt2 += (double)xc1[r] * (double)bv;
+              pn += xc1[r] * qv;
+              pd += xc1[r] * bv;
             } else {
               A corr;
               if (use_invd)
@@ -277,12 +281,14 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
                 corr = __fdividef(bv - Ax, D);
               else
                 corr = (bv - Ax) / D;
-              const A xn = dirn ? xc1[r] : xc1[r] + (A)a.omega * corr;
+              const A xn = dirn ? xc1[r] : xc1[r] + omega * corr;
               out[idx] = from_acc<T>(xn);
             }
           }
         }
       }
+      if (OP == OP_RESIDUAL || OP == OP_MATVEC) nrm += pn;
+      if (OP == OP_MATVEC) dt2 += pd;
     }
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
@@ -316,8 +322,8 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
     __syncthreads();
     return false;
   }
-  if ((OP == OP_RESIDUAL || OP == OP_MATVEC) && a.norm2 != nullptr) block_sum_atomic(nrm, a.norm2, red);
-  if (OP == OP_MATVEC && a.dot2 != nullptr) block_sum_atomic(dt2, a.dot2, red);
+  if ((OP == OP_RESIDUAL || OP == OP_MATVEC) && a.norm2 != nullptr) block_sum_atomic((double)nrm, a.norm2, red);
+  if (OP == OP_MATVEC && a.dot2 != nullptr) block_sum_atomic((double)dt2, a.dot2, red);
   __syncthreads();  // stage buffers are free for the next tile
   return true;
 }

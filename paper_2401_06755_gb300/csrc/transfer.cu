@@ -11,90 +11,149 @@ __device__ __forceinline__ bool dir_node(const LevelGeom& g, int i, int j, int k
          (g.dir[3] && j == g.ny - 1) || (g.dir[4] && k == 0) || (g.dir[5] && k == g.nz - 1);
 }
 
-// One thread per coarse node: r_c(I) = sum_{d in {-1,0,1}^3} prod_d (1/2)^|d| r_f(2I + d) over
-// the fine nodes that exist; zero at coarse Dirichlet nodes.  Separable: x, then y, then z.
-template <typename T>
-__global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ rc, const LevelGeom gf,
-                           const LevelGeom gc) {
-  using A = typename Acc<T>::type;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  const int K = blockIdx.z;
-  if (I >= gc.nx || J >= gc.ny) return;
-  A acc = A(0);
-  if (!dir_node(gc, I, J, K)) {
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int k = 2 * K + dz;
-      if (k < 0 || k >= gf.nz) continue;
-      A az = A(0);
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int j = 2 * J + dy;
-        if (j < 0 || j >= gf.ny) continue;
-        const T* row = rf + gf.pitch * ((long long)j + (long long)gf.ny * k);
-        const int i = 2 * I;
-        A ax = to_acc(row[i]);
-        if (i > 0) ax += A(0.5) * to_acc(row[i - 1]);
-        if (i + 1 < gf.nx) ax += A(0.5) * to_acc(row[i + 1]);
-        az += (dy == 0 ? A(1) : A(0.5)) * ax;
-      }
-      acc += (dz == 0 ? A(1) : A(0.5)) * az;
-    }
-  }
-  rc[I + gc.pitch * ((long long)J + (long long)gc.ny * K)] = from_acc<T>(acc);
+// Pairs of consecutive nodes (an even first index on a row of even pitch: aligned) as one load.
+__device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
+  const double2 t = *reinterpret_cast<const double2*>(p);
+  a = t.x, b = t.y;
+}
+__device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
+  const float2 t = *reinterpret_cast<const float2*>(p);
+  a = t.x, b = t.y;
+}
+__device__ __forceinline__ void ld2(const bf16* p, float& a, float& b) {
+  const float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  a = t.x, b = t.y;
+}
+__device__ __forceinline__ void st2(double* p, double a, double b) { *reinterpret_cast<double2*>(p) = make_double2(a, b); }
+__device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+__device__ __forceinline__ void st2(bf16* p, float a, float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
 }
 
-// One thread per fine node: e_f(i) (+)= sum over the coarse nodes bracketing i of
-// prod_d (1 at an even index, 1/2 for each of the two parents at an odd index) e_c.
-// One thread per fine (i, j) column and a run of kPz fine planes: e_f (+)= sum over the coarse
-// nodes bracketing each fine node of prod_d (1 at an even index, 1/2 for each of the two parents
-// at an odd index) e_c.
+// Restriction r_c(I) = sum_{d in {-1,0,1}^3} prod_d (1/2)^|d| r_f(2I + d) over the fine nodes that
+// exist; zero at coarse Dirichlet nodes.  A thread owns coarse column (I, J) over kRz coarse
+// planes (unrolled, so all its loads are in flight together); lane I loads the fine pair
+// (2I, 2I+1) of each row and the node 2I-1.  Consecutive coarse planes share a fine plane, read
+// once.
+constexpr int kRz = 2;
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_restrict(const T* __restrict__ rf, T* __restrict__ rc, const LevelGeom gf,
+                                                  const LevelGeom gc) {
+  using A = typename Acc<T>::type;
+  const int lane = threadIdx.x;
+  const int I = blockIdx.x * 32 + lane;
+  const int J = blockIdx.y * 4 + threadIdx.y;
+  if (J >= gc.ny) return;  // whole warps only: the shuffles below need every lane
+  const int i0 = 2 * min(I, gc.nx - 1);
+  const bool has_r = i0 + 1 < gf.nx;
+  // x-weighted sum of fine row (j, k) at column I
+  // every lane loads its own left neighbour (same cache lines as the pairs): no lane-dependent
+  // branch, so the loads of all rows and planes are in flight together
+  const int il = i0 > 0 ? i0 - 1 : 0;
+  const A wl = i0 > 0 ? A(0.5) : A(0), wr = has_r ? A(0.5) : A(0);
+  auto xsum = [&](long long rowoff) -> A {
+    const T* row = rf + rowoff;
+    A c, r;
+    ld2(row + i0, c, r);
+    const A l = to_acc(row[il]);
+    return c + wl * l + (has_r ? wr * r : A(0));
+  };
+  const int j0 = 2 * J;
+  const bool has_jm = J > 0, has_jp = j0 + 1 < gf.ny;
+  auto psum = [&](int k) -> A {  // fine plane k, weighted over rows 2J-1, 2J, 2J+1
+    const long long pk = (long long)gf.ny * k;
+    A v = xsum(gf.pitch * (pk + j0));
+    A side = A(0);
+    if (has_jm) side += xsum(gf.pitch * (pk + j0 - 1));
+    if (has_jp) side += xsum(gf.pitch * (pk + j0 + 1));
+    return v + A(0.5) * side;
+  };
+  const int K0 = blockIdx.z * kRz, K1 = min(gc.nz, K0 + kRz);
+  A prev = K0 > 0 ? psum(2 * K0 - 1) : A(0);
+  const bool dxy = (gc.dir[0] && I == 0) || (gc.dir[1] && I == gc.nx - 1) || (gc.dir[2] && J == 0) ||
+                   (gc.dir[3] && J == gc.ny - 1);
+#pragma unroll
+  for (int K = K0; K < K0 + kRz; ++K) {
+    if (K >= K1) break;
+    const A p0 = psum(2 * K);
+    const A p1 = 2 * K + 1 < gf.nz ? psum(2 * K + 1) : A(0);
+    const A v = p0 + A(0.5) * (prev + p1);
+    prev = p1;
+    const bool dn = dxy || (gc.dir[4] && K == 0) || (gc.dir[5] && K == gc.nz - 1);
+    if (I < gc.nx) rc[I + gc.pitch * ((long long)J + (long long)gc.ny * K)] = from_acc<T>(dn ? A(0) : v);
+  }
+}
+
+// Prolongation e_f (+)= P e_c: each fine node takes the coarse nodes bracketing it, weight 1 at an
+// even index and 1/2 for each of the two parents at an odd index, per axis.  A thread owns the
+// fine pair (2I, 2I+1) of row j over kPz fine planes: x-even = e_c(I), x-odd = (e_c(I) + e_c(I+1))/2.
+// Dirichlet fine nodes keep base (or 0).
 constexpr int kPz = 8;
 
 template <typename T>
-__global__ void k_prolong(const T* __restrict__ ec, T* ef, const T* base, const LevelGeom gc,
-                          const LevelGeom gf) {
+__global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ ec, T* ef, const T* base, const LevelGeom gc,
+                                                 const LevelGeom gf) {
   using A = typename Acc<T>::type;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= gf.nx || j >= gf.ny) return;
-  const int I0 = i >> 1, J0 = j >> 1;
-  const int I1 = I0 + (i & 1), J1 = J0 + (j & 1);
-  const A wxy = ((i & 1) ? A(0.5) : A(1)) * ((j & 1) ? A(0.5) : A(1));
-  const bool dxy = (gf.dir[0] && i == 0) || (gf.dir[1] && i == gf.nx - 1) || (gf.dir[2] && j == 0) ||
-                   (gf.dir[3] && j == gf.ny - 1);
-  // in-plane interpolation of coarse plane K at (i, j)
-  auto plane = [&](int K) {
+  const int lane = threadIdx.x;
+  const int I = blockIdx.x * 32 + lane;
+  const int j = blockIdx.y * 4 + threadIdx.y;
+  if (j >= gf.ny) return;  // whole warps only
+  const int Ic = min(I, gc.nx - 1);
+  const bool has_next = Ic + 1 < gc.nx;
+  const int J0 = j >> 1, J1 = J0 + (j & 1);
+  // (x-even, x-odd) values of coarse plane K at fine row j
+  // rows J0 and J1 (= J0 for an even j, weight 1/2 each then): the branch-free sum of both
+  const int In = has_next ? Ic + 1 : Ic;
+  auto plane = [&](int K, A& ve, A& vo) {
     const T* p = ec + gc.pitch * (long long)gc.ny * K;
-    A v = to_acc(p[I0 + gc.pitch * (long long)J0]);
-    if (i & 1) v += to_acc(p[I1 + gc.pitch * (long long)J0]);
-    if (j & 1) {
-      A t = to_acc(p[I0 + gc.pitch * (long long)J1]);
-      if (i & 1) t += to_acc(p[I1 + gc.pitch * (long long)J1]);
-      v += t;
-    }
-    return v * wxy;
+    const T* r0 = p + gc.pitch * (long long)J0;
+    const T* r1 = p + gc.pitch * (long long)J1;
+    const A a = A(0.5) * (to_acc(r0[Ic]) + to_acc(r1[Ic]));
+    const A an = A(0.5) * (to_acc(r0[In]) + to_acc(r1[In]));
+    ve = a;
+    vo = A(0.5) * (a + an);
   };
   const int k0 = blockIdx.z * kPz, k1 = min(gf.nz, k0 + kPz);
-  // coarse planes k0/2 .. k0/2 + kPz/2 interpolated in-plane first (independent loads)
-  A cp[kPz / 2 + 1];
   const int K0 = k0 >> 1;
+  A ce[kPz / 2 + 1], co[kPz / 2 + 1];
 #pragma unroll
-  for (int t = 0; t <= kPz / 2; ++t) cp[t] = (K0 + t < gc.nz) ? plane(K0 + t) : A(0);
+  for (int t = 0; t <= kPz / 2; ++t) {
+    if (K0 + t < gc.nz) {
+      plane(K0 + t, ce[t], co[t]);
+    } else {
+      ce[t] = co[t] = A(0);
+    }
+  }
+  const int i = 2 * I;
+  const bool ok0 = I < gc.nx, ok1 = i + 1 < gf.nx;
+  const bool dy = (gf.dir[2] && j == 0) || (gf.dir[3] && j == gf.ny - 1);
+  const bool d0x = (gf.dir[0] && i == 0) || (gf.dir[1] && i == gf.nx - 1);
+  const bool d1x = gf.dir[1] && i + 1 == gf.nx - 1;
 #pragma unroll
   for (int t = 0; t < kPz; ++t) {
     const int k = k0 + t;
     if (k >= k1) break;
-    const A v0 = (t & 1) ? A(0.5) * (cp[t >> 1] + cp[(t >> 1) + 1]) : cp[t >> 1];
-    const long long idx = i + gf.pitch * ((long long)j + (long long)gf.ny * k);
-    const bool dn = dxy || (gf.dir[4] && k == 0) || (gf.dir[5] && k == gf.nz - 1);
-    if (dn) {
-      ef[idx] = base ? base[idx] : from_acc<T>(A(0));
-      continue;
+    A v0 = (t & 1) ? A(0.5) * (ce[t >> 1] + ce[(t >> 1) + 1]) : ce[t >> 1];
+    A v1 = (t & 1) ? A(0.5) * (co[t >> 1] + co[(t >> 1) + 1]) : co[t >> 1];
+    const bool dz = dy || (gf.dir[4] && k == 0) || (gf.dir[5] && k == gf.nz - 1);
+    T* out = ef + i + gf.pitch * ((long long)j + (long long)gf.ny * k);
+    A b0 = A(0), b1 = A(0);
+    if (base) {
+      const T* bp = base + (out - ef);
+      if (ok1) {
+        ld2(bp, b0, b1);
+      } else if (ok0) {
+        b0 = to_acc(bp[0]);
+      }
     }
-    const A v = base ? v0 + to_acc(base[idx]) : v0;
-    ef[idx] = from_acc<T>(v);
+    v0 = (dz || d0x) ? b0 : v0 + b0;
+    v1 = (dz || d1x) ? b1 : v1 + b1;
+    if (ok1) {
+      st2(out, v0, v1);
+    } else if (ok0) {
+      out[0] = from_acc<T>(v0);
+    }
   }
 }
 
@@ -200,8 +259,10 @@ __global__ void k_prolong_batch(const BatchXfer* __restrict__ tab, int count, in
 
 template <typename T>
 int restrict_t(const void* rf, const LevelGeom& gf, void* rc, const LevelGeom& gc, cudaStream_t s) {
+  if ((gf.pitch & 1) || (reinterpret_cast<uintptr_t>(rf) % (2 * sizeof(T))))
+    return set_error(NN4_EINVAL, "restriction needs an even row pitch and an aligned fine field");
   dim3 blk(32, 4);
-  dim3 grd((gc.nx + 31) / 32, (gc.ny + 3) / 4, gc.nz);
+  dim3 grd((gc.nx + 31) / 32, (gc.ny + 3) / 4, (gc.nz + kRz - 1) / kRz);
   k_restrict<T><<<grd, blk, 0, s>>>(static_cast<const T*>(rf), static_cast<T*>(rc), gf, gc);
   return check_cuda(cudaGetLastError(), "restrict launch");
 }
@@ -209,8 +270,11 @@ int restrict_t(const void* rf, const LevelGeom& gf, void* rc, const LevelGeom& g
 template <typename T>
 int prolong_t(const void* ec, const LevelGeom& gc, void* ef, const void* base, const LevelGeom& gf,
               cudaStream_t s) {
+  if ((gf.pitch & 1) || (reinterpret_cast<uintptr_t>(ef) % (2 * sizeof(T))) ||
+      (base && reinterpret_cast<uintptr_t>(base) % (2 * sizeof(T))))
+    return set_error(NN4_EINVAL, "prolongation needs an even row pitch and aligned fine fields");
   dim3 blk(32, 4);
-  dim3 grd((gf.nx + 31) / 32, (gf.ny + 3) / 4, (gf.nz + kPz - 1) / kPz);
+  dim3 grd((gc.nx + 31) / 32, (gf.ny + 3) / 4, (gf.nz + kPz - 1) / kPz);
   k_prolong<T><<<grd, blk, 0, s>>>(static_cast<const T*>(ec), static_cast<T*>(ef), static_cast<const T*>(base), gc, gf);
   return check_cuda(cudaGetLastError(), "prolong launch");
 }
