@@ -156,6 +156,69 @@ def config_dict(args):
             "l2": "inputs larger than L2 (b, x, k: 3 x 144 MB FP64 plus the hierarchy)"}
 
 
+# ---------------------------------------------------------------- ncu summaries
+# ncu kernel names (template arguments spelled plainly) -> the bench's kernel names.  Several
+# levels share a kernel; the group (same name and grid) with the most time is the finest level.
+NCU_NAMES = [
+    (r"k_pass<double, 3,", "pass64:matvec"), (r"k_pass<double, 1,", "pass64:residual"),
+    (r"k_pass<__nv_bfloat16, 2, 2,", "pass:jacobi:L0"), (r"k_pass<float, 3,", "inner:matvec"),
+    (r"k_fcg_update<float, __nv_bfloat16>", "inner:update"),
+    (r"k_new_direction<__nv_bfloat16, float>", "inner:direction"),
+    (r"k_dot_zq<__nv_bfloat16, float>", "inner:dot"), (r"k_restrict<__nv_bfloat16>", "restrict:L0"),
+    (r"k_prolong<__nv_bfloat16>", "prolong:L0"), (r"k_pass27<__nv_bfloat16, 2>", "pass27:jacobi:L1"),
+    (r"k_coarse<__nv_bfloat16>", "coarse_levels"),
+]
+
+
+def ncu_summary(path, write_traffic):
+    """Per-kernel launches, time and share of an ncu CSV (one row per launch and metric), as a
+    markdown table; with DRAM byte counters, also the per-launch traffic of the bench kernels
+    (written to profiles/ncu_traffic.json with the hash of each kernel's source file)."""
+    import collections
+    import csv
+    import hashlib
+    import re
+    lines = [ln for ln in open(path) if not ln.startswith("==")]
+    launches = collections.OrderedDict()
+    for r in csv.DictReader(lines):
+        key = (r["ID"], r["Kernel Name"], r["Grid Size"])
+        v = float(r["Metric Value"].replace(",", ""))
+        unit = r["Metric Unit"]
+        scale = {"ns": 1e-3, "usecond": 1.0, "us": 1.0, "ms": 1e3, "byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6,
+                 "Gbyte": 1e9}.get(unit, 1.0)
+        launches.setdefault(key, {})[r["Metric Name"]] = v * scale
+    groups = collections.OrderedDict()
+    for (lid, name, grid), m in launches.items():
+        base = re.sub(r"\(.*", "", name).replace("void ", "").replace("<unnamed>::", "").replace("unnamed>::", "").replace("nn4::", "")
+        g = groups.setdefault((base, grid), {"n": 0, "us": 0.0, "dram": 0.0})
+        g["n"] += 1
+        g["us"] += m.get("gpu__time_duration.sum", 0.0)
+        g["dram"] += m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
+    total = sum(g["us"] for g in groups.values())
+    print(f"| kernel | grid | launches | total us | share | avg us | DRAM MB/launch |")
+    print("|---|---|---|---|---|---|---|")
+    for (base, grid), g in sorted(groups.items(), key=lambda kv: -kv[1]["us"]):
+        print(f"| `{base[:60]}` | {grid} | {g['n']} | {g['us']:.1f} | {g['us'] / total:.4f} | "
+              f"{g['us'] / g['n']:.2f} | {g['dram'] / g['n'] / 1e6:.2f} |")
+    print(f"\ntotal {total:.1f} us over {sum(g['n'] for g in groups.values())} launches")
+    if not write_traffic:
+        return
+    out = {}
+    for pat, bname in NCU_NAMES:
+        cands = [(g["us"], g) for (base, grid), g in groups.items() if base.startswith(pat)]
+        if not cands or max(c[1]["dram"] for c in cands) <= 0:
+            continue
+        g = max(cands, key=lambda c: c[0])[1]
+        src = KERNEL_SOURCE[bname]
+        with open(os.path.join(ROOT, "paper_2401_06755_gb300", "csrc", src), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        out[bname] = {"dram_bytes_per_launch": g["dram"] / g["n"], "launches": g["n"], "source": src,
+                      "source_sha256": sha}
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json"), "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+        f.write("\n")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,14 +227,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--inner", default="bf16", choices=["bf16", "f32"])
     ap.add_argument("--m", type=int, default=1, help="V-cycles per outer iteration (or per inner iteration)")
-    ap.add_argument("--krylov", type=int, default=12, help="inner FP32 flexible-CG iterations (0: none)")
+    ap.add_argument("--krylov", type=int, default=10, help="inner FP32 flexible-CG iterations (0: none)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--ref-n", type=int, default=65)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time the mixed solve only (for profiler runs; no JSON contract)")
     ap.add_argument("--n", type=int, default=N_NODES, help="nodes per axis (profiler runs on smaller cases)")
+    ap.add_argument("--ncu-summary", metavar="CSV", help="summarise an ncu launch list of the timed region")
+    ap.add_argument("--write-traffic", action="store_true", help="with --ncu-summary: write profiles/ncu_traffic.json")
     args = ap.parse_args()
+    if args.ncu_summary:
+        ncu_summary(args.ncu_summary, args.write_traffic)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -298,10 +366,11 @@ def main():
     total_prof = sum(v[1] for v in prof.values())
     top = max(prof.items(), key=lambda kv: kv[1][1])
     roof = roofline_entry(top, n, MEASURED.get("fp64_tflops", 1.20), MEASURED.get("hbm_gbs", 6674.5))
-    inner_kernels = {kk: vv for kk, vv in prof.items() if kk.startswith("pass:") and kk.endswith(":L0")}
-    inner_top = max(inner_kernels.items(), key=lambda kv: kv[1][1]) if inner_kernels else None
-    roof_inner = roofline_entry(inner_top, n, 0, MEASURED.get("hbm_gbs", 6674.5),
-                                dtype=args.inner) if inner_top else None
+    roof_all = [roofline_entry(kv, n, MEASURED.get("fp64_tflops", 1.20), MEASURED.get("hbm_gbs", 6674.5))
+                for kv in sorted(prof.items(), key=lambda kv: -kv[1][1])
+                if kv[0] in FLOPS_PER_NODE or (kv[0] in BYTES_PER_NODE and args.inner == "bf16")]
+    for r in roof_all:
+        r["share"] = round(prof[r["kernel"]][1] / total_prof, 4)
 
     batched = {"mixed": run_batched(nn4, torch, inner, 2, max(1, args.steps // 2), 1),
                "f64": run_batched(nn4, torch, nn4.F64, 1, 1, 1)}
@@ -327,7 +396,7 @@ def main():
             "fp64_path": {"solves_per_s": 1000.0 / ms64, "ms_per_solve": ms64, "iterations": i64["iterations"]},
             "speedup_vs_fp64": (1000.0 / ms_per) / (1000.0 / ms64),
             "vcycle_ms": {args.inner: vc_inner, "f64": vc_64},
-            "roofline": roof, "roofline_inner": roof_inner,
+            "roofline": roof, "roofline_kernels": roof_all,
             "kernel_shares": {kk: round(vv[1] / total_prof, 4) for kk, vv in
                               sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]},
             "batched": batched, "column_step": column,
@@ -429,31 +498,65 @@ def _load_peaks():
 
 MEASURED = _load_peaks()
 
-# Algorithmic work per fine node ("Roofline accounting"):
-#  FP64 matvec of Eq. k-T with the sum-factorised interior stencil: L x and L (k x) and L k at
-#  23 flops each (8 neighbour-class multiply-adds on 7 partial sums), plus 7 flops to combine
-#  -> 76 FP64 flops per node.  Inner stencil passes move (fields read + written) x storage bytes.
-FLOPS_PER_NODE = {"pass64:matvec": 76.0, "pass64:residual": 77.0}
-FIELDS_PER_NODE = {"pass:residual:L0": 4, "pass:jacobi:L0": 4, "restrict:L0": 1.125, "prolong:L0": 2.125}
-STORE = {"bf16": 2, "f32": 4}
+# Algorithmic work per node of the level a kernel runs on.
+#  FP64 mat-vec of Eq. k-T, sum-factorised, isotropic spacing, L k read pointwise (RY = 4 rows a
+#  thread): L x 13.5 flops (x-neighbour sums 1.5, y sums 2, the two class sums 8, z running sums
+#  2), L(k x) 18 (the k x products add 6 per node), the combination 9, the two dot products 4
+#  -> 44.5 flops; the residual form 43.5 (b - A x, its square).  An FMA counts 2.
+#  Streaming kernels: bytes read + written per node of their level.
+FLOPS_PER_NODE = {"pass64:matvec": 44.5, "pass64:residual": 43.5}
+BYTES_PER_NODE = {
+    "pass:jacobi:L0": 10.0,    # BF16: x (haloed), k, b, L k read; e written
+    "inner:matvec": 20.0,      # FP32: p (haloed), k, L k, r read; q written
+    "inner:update": 26.0,      # FP32 x, r, p, q read; x, r written; BF16 copy of r written
+    "inner:direction": 10.0,   # BF16 z and FP32 p_old read; FP32 p written
+    "inner:dot": 6.0,          # BF16 z and FP32 q read
+    "restrict:L0": 2.25,       # per fine node: BF16 fine read, 1/8 coarse written
+    "prolong:L0": 2.25,        # per fine node: BF16 fine written, 1/8 coarse read
+    "pass27:jacobi:L1": 60.0,  # per L1 node: 27 BF16 coefficients, x (haloed), b read, e written
+}
+LEVEL = {"pass27:jacobi:L1": 1}  # kernels that run on level 1 ((n+1)/2 nodes per axis)
+KERNEL_SOURCE = {"pass64:matvec": "stencil.cu", "pass64:residual": "stencil.cu", "pass:jacobi:L0": "stencil.cu",
+                 "inner:matvec": "stencil.cu", "inner:update": "outer.cu", "inner:direction": "outer.cu",
+                 "inner:dot": "outer.cu", "restrict:L0": "transfer.cu", "prolong:L0": "transfer.cu",
+                 "pass27:jacobi:L1": "galerkin.cu", "coarse_levels": "tail.cu"}
 
 
-def roofline_entry(item, n, fp64_tflops, hbm_gbs, dtype=None):
+def _traffic(name):
+    """DRAM bytes per launch from the committed ncu summary, or None when the kernel's source has
+    changed since the capture (the file hash is recorded with it)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f).get(name)
+    except (OSError, ValueError):
+        return None
+    src = KERNEL_SOURCE.get(name)
+    if not rec or not src:
+        return None
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2401_06755_gb300", "csrc", src), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != rec.get("source_sha256"):
+            return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def roofline_entry(item, n, fp64_tflops, hbm_gbs):
     name, (launches, total_ms) = item
     avg_ms = total_ms / max(1, launches)
-    nodes = float(n) ** 3
+    nodes = float((n + 1) // 2 if LEVEL.get(name) == 1 else n) ** 3
     if name in FLOPS_PER_NODE:
         achieved = FLOPS_PER_NODE[name] * nodes / (avg_ms * 1e-3) / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
-                "frac": achieved / fp64_tflops, "traffic": None, "avg_ms": avg_ms,
-                "peak_note": "FP64 FMA pipe, measured 1.20 TFLOP/s on this GB300 (2 FP64 FMA/clk/SM x 152 SMs)"}
-    if name in FIELDS_PER_NODE:
-        s = STORE.get(dtype, 8)
-        gbs = FIELDS_PER_NODE[name] * s * nodes / (avg_ms * 1e-3) / 1e9
+                "frac": achieved / fp64_tflops, "traffic": _traffic(name), "avg_ms": avg_ms,
+                "algorithmic": f"{FLOPS_PER_NODE[name]} FP64 flops x {int(nodes)} nodes",
+                "peak_note": "FP64 FMA pipe of this GB300, measured 1.20 TFLOP/s (DFMA loop)"}
+    if name in BYTES_PER_NODE:
+        gbs = BYTES_PER_NODE[name] * nodes / (avg_ms * 1e-3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
-                "frac": gbs / hbm_gbs, "traffic": None, "avg_ms": avg_ms, "peak_note": "of measured copy bandwidth"}
+                "frac": gbs / hbm_gbs, "traffic": _traffic(name), "avg_ms": avg_ms,
+                "algorithmic": f"{BYTES_PER_NODE[name]} B x {int(nodes)} nodes",
+                "peak_note": "of measured copy bandwidth (MEASURED_PEAKS hbm_gbs)"}
     return {"kernel": name, "bound": None, "avg_ms": avg_ms}
-
 
 if __name__ == "__main__":
     main()

@@ -121,6 +121,25 @@ __global__ void k_to_inner(const double* __restrict__ r, LevelGeom g64, T* __res
   }
 }
 
+// r = b at free nodes, 0 at Dirichlet nodes (the residual of a zero initial guess)
+__global__ void k_masked_copy(const double* __restrict__ b, double* __restrict__ r, LevelGeom g) {
+  NN4_FOR_NODES(g) {
+    const long long o = row * g.pitch + i;
+    r[o] = dirichlet_row(g, row, i) ? 0.0 : b[o];
+  }
+}
+
+// out += sum of v^2 over every node
+__global__ void k_sumsq(const double* __restrict__ v, LevelGeom g, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  NN4_FOR_NODES(g) {
+    const double t = v[row * g.pitch + i];
+    s += t * t;
+  }
+  block_sum_atomic(s, out, red);
+}
+
 __global__ void k_norm_masked(const double* __restrict__ v, LevelGeom g, double* out) {
   __shared__ double red[32];
   double s = 0.0;
@@ -306,6 +325,14 @@ int launch_inv_diag(const double* k, const double* lk, double* invd, const Level
   return check_cuda(cudaGetLastError(), "inverse diagonal");
 }
 
+int launch_masked_copy(const double* b, double* r, const LevelGeom& g, cudaStream_t s) {
+  k_masked_copy<<<pw_grid(g), kPwBlock, 0, s>>>(b, r, g);
+  return check_cuda(cudaGetLastError(), "masked copy");
+}
+int launch_sumsq(const double* v, const LevelGeom& g, double* out, cudaStream_t s) {
+  k_sumsq<<<pw_grid(g), kPwBlock, 0, s>>>(v, g, out);
+  return check_cuda(cudaGetLastError(), "sum of squares");
+}
 int launch_norm_masked(const double* v, const LevelGeom& g, double* out, cudaStream_t s) {
   k_norm_masked<<<pw_grid(g), kPwBlock, 0, s>>>(v, g, out);
   return check_cuda(cudaGetLastError(), "norm");

@@ -14,6 +14,10 @@ int launch_to_inner(nn4_dtype dt, const double* r, const LevelGeom& g64, void* r
 // invd = 1 / diag(A) for Eq. k-T from k and lk = L k (FP64)
 int launch_inv_diag(const double* k, const double* lk, double* invd, const LevelGeom& g, double c0,
                     cudaStream_t s);
+// r = b at free nodes, 0 at Dirichlet nodes
+int launch_masked_copy(const double* b, double* r, const LevelGeom& g, cudaStream_t s);
+// out += sum of v^2 over all nodes
+int launch_sumsq(const double* v, const LevelGeom& g, double* out, cudaStream_t s);
 // out += sum of v^2 over free nodes
 int launch_norm_masked(const double* v, const LevelGeom& g, double* out, cudaStream_t s);
 // out += z . q

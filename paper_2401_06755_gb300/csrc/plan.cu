@@ -988,11 +988,27 @@ int solve_device(PlanImpl* P, double rtol, int32_t max_iters, nn4_solve_info* in
     P->hist_cap = cap;
   }
   if ((rc = ensure_graphs(P))) return rc;
-  // ||b||^2 over free nodes, initial residual
-  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 1, 0, sizeof(double), s), "zero"))) return rc;
+  // ||b||^2 over free nodes and ||x0||^2; the initial residual of x0 = 0 is b itself (zero at
+  // Dirichlet nodes), which saves the FP64 residual pass
+  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 1, 0, sizeof(double), s), "zero")) ||
+      (rc = check_cuda(cudaMemsetAsync(P->scal + 7, 0, sizeof(double), s), "zero")))
+    return rc;
   const int64_t kstart = P->kernels;
-  if ((rc = K(P, "pointwise:norm", s, [&] { return launch_norm_masked(P->b64, P->g64, P->scal + 1, s); }))) return rc;
-  if ((rc = outer_residual(P, s, P->scal + 0))) return rc;
+  if ((rc = K(P, "pointwise:norm", s, [&] { return launch_norm_masked(P->b64, P->g64, P->scal + 1, s); })) ||
+      (rc = K(P, "pointwise:norm", s, [&] { return launch_sumsq(P->x64, P->g64, P->scal + 7, s); })))
+    return rc;
+  double xx = 1.0;
+  if ((rc = check_cuda(cudaMemcpyAsync(P->host_hist, P->scal + 7, sizeof(double), cudaMemcpyDeviceToHost, s), "read")) ||
+      (rc = check_cuda(cudaStreamSynchronize(s), "sync")))
+    return rc;
+  xx = P->host_hist[0];
+  if (xx == 0.0) {
+    if ((rc = K(P, "pointwise:copy", s, [&] { return launch_masked_copy(P->b64, P->r64, P->g64, s); })) ||
+        (rc = check_cuda(cudaMemcpyAsync(P->scal + 0, P->scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s), "r.r")))
+      return rc;
+  } else if ((rc = outer_residual(P, s, P->scal + 0))) {
+    return rc;
+  }
   if (P->o.outer == NN4_OUTER_FCG) {
     // r64 holds the residual; rT for the first inner solve; p_old = q_old = 0, p.q_old = 1
     nn4_dtype tt;

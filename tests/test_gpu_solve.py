@@ -101,6 +101,32 @@ def test_solve_fp64_fixed_cycles_history():
         assert _rel(nn4.nodes(X, G).cpu().numpy(), xo) <= 1e-12
 
 
+@pytest.mark.parametrize("outer", ["cycles", "fcg"])
+def test_solve_fp64_warm_start(outer):
+    """A nonzero initial guess (also on Dirichlet nodes, which enter A x0 at their neighbours)
+    takes the residual path; a zero one the copy path: both match the oracle."""
+    need_gpu()
+    nn4 = _nn4()
+    g, G = _grids((33, 17, 33), (1 / 32,) * 3, (True, False, False, False, True, True))
+    b = _rhs(g, 5)
+    b[mg.dirichlet_mask(g)] = 0.0
+    x0 = 0.1 * standard_normal(6, int(np.prod(g.shape))).reshape(g.shape)
+    for start in (x0, np.zeros(g.shape)):
+        if outer == "cycles":
+            xo, ho = mg.pressure_solve(g, b, x0=start, fixed_cycles=8)
+            plan = nn4.Plan(G)
+            iters = 8
+        else:
+            xo, ho = mg.pressure_solve_fcg(g, b, x0=start, rtol=0.0, max_iters=6)
+            plan = nn4.Plan(G, outer=nn4.OUTER_FCG)
+            iters = 6
+        B, X = nn4.to_field(b, G), nn4.to_field(start, G)
+        info = plan.solve(B, X, rtol=0.0, max_iters=iters)
+        hg = np.array(info["history"])
+        assert np.all(np.abs(hg - np.array(ho[:len(hg)])) <= 1e-12 + 1e-9 * np.array(ho[:len(hg)]))
+        assert _rel(nn4.nodes(X, G).cpu().numpy(), xo) <= 1e-11
+
+
 @pytest.mark.parametrize("inner", ["f32", "bf16"])
 @pytest.mark.parametrize("outer", ["cycles", "fcg"])
 def test_solve_mixed_constant_coefficient(inner, outer):
