@@ -56,11 +56,11 @@ def test_batched_fp64_matches_oracle_cycles():
         assert np.linalg.norm(xg - xo) <= 1e-12 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("inner", ["f32", "bf16"])
-def test_batched_mixed_reaches_fp64_solutions(inner):
+@pytest.mark.parametrize("inner,cycles", [("f32", 2), ("f32", 4), ("bf16", 2)])
+def test_batched_mixed_reaches_fp64_solutions(inner, cycles):
     need_gpu()
     nn4, gs, Gs, bs = _setup(10)
-    batch = nn4.Batch(Gs, inner=nn4.F32 if inner == "f32" else nn4.BF16, inner_cycles=2)
+    batch = nn4.Batch(Gs, inner=nn4.F32 if inner == "f32" else nn4.BF16, inner_cycles=cycles)
     B = [nn4.to_field(b, G) for b, G in zip(bs, Gs)]
     X = [nn4.field(G) for G in Gs]
     code, infos, lat = batch.solve(B, X, rtol=1e-10, max_iters=100)
