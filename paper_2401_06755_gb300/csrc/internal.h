@@ -43,6 +43,12 @@ struct PassArgs {
   // on-the-fly stencil of k; invd = 1 / diag(A) replaces the division in Jacobi.
   const void* lk;
   const void* invd;
+  // OP_JACOBI only (optional): dq_out += sum over nodes of (the new x rounded to the storage type)
+  // times dq, an FP32 field read through its own tensor map (the flexible-CG dot z.q_old fused
+  // into the sweep that produces z)
+  const float* dq;
+  long long dq_pitch;  // row pitch of dq (elements)
+  double* dq_out;
 };
 
 // Stencil pass launch configuration (chosen by the autotuner or by default).
@@ -75,7 +81,7 @@ unsigned int tail_error_word();
 // ---------------------------------------------------------------- launchers
 // Tensor maps of one stencil pass: haloed tiles of x and k, pointwise tiles of b, L k, 1/diag.
 struct PassMaps {
-  CUtensorMap x, k, b, lk, invd;
+  CUtensorMap x, k, b, lk, invd, dq;
 };
 
 // One instance's part of a batched stencil pass (device table entry, 64-byte aligned maps).

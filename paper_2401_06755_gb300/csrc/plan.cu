@@ -35,6 +35,7 @@ struct Level {
   void* e = nullptr;  // correction (output of the Jacobi sweep)
   void* t = nullptr;  // prolongated correction / fine residual (input of the Jacobi sweep)
   PassMaps m_jac{}, m_res{};  // Jacobi (x = t, b = r) and residual (x = e, b = r) passes
+  PassMaps m_jac_dq[2]{};     // level 0 with the inner Krylov loop: Jacobi + the fused dot with q[parity]
   void* a27 = nullptr;  // Galerkin coefficients (coefficient field, levels >= 1)
   void* k = nullptr;    // coefficient field in the inner type (level 0)
 };
@@ -487,6 +488,8 @@ struct Fine {
   void* e;
   const PassMaps* res_maps;  // residual pass on (e, r); NULL: built per launch
   const PassMaps* jac_maps;  // level-0 Jacobi pass (t, r); NULL: built per launch
+  const float* dq = nullptr;  // optional: the final level-0 sweep also adds e.dq to *dq_out
+  double* dq_out = nullptr;
 };
 
 // Level-l residual / Jacobi pass.  Level 0 with a coefficient field uses k (and, for FP64
@@ -508,10 +511,13 @@ PassArgs level_args(PlanImpl* P, int l, const void* b, void* out) {
 }
 
 int run_pass(PlanImpl* P, int l, int op, const void* x, const PassMaps* maps, const void* b, void* out,
-             cudaStream_t s, double* norm2 = nullptr) {
+             cudaStream_t s, double* norm2 = nullptr, const float* dq = nullptr, double* dq_out = nullptr) {
   Level& L = P->lv[l];
   PassArgs a = level_args(P, l, b, out);
   a.norm2 = norm2;
+  a.dq = dq;
+  a.dq_pitch = P->g32.pitch;
+  a.dq_out = dq_out;
   if (P->vc && l > 0)
     return K(P, std::string("pass27:") + opname(op) + ":" + lvl(l), s,
              [&] { return launch_pass27(P->T, op, a, x, L.a27, s); });
@@ -590,18 +596,30 @@ int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
          return launch_prolong_base(T, P->lv[1].e, P->lv[1].g, L0.t, first ? nullptr : F.e, L0.g, s);
        })))
     return rc;
-  return run_pass(P, 0, OP_JACOBI, L0.t, F.jac_maps, F.r, F.e, s);
+  return run_pass(P, 0, OP_JACOBI, L0.t, F.jac_maps, F.r, F.e, s, nullptr, F.dq, F.dq_out);
 }
 
 // ---------------------------------------------------------------- outer iterations
-int inner_solve(PlanImpl* P, cudaStream_t s) {
+// inner_cycles V-cycles on A e = r at level 0 from e = 0.  dq_par >= 0 (inner Krylov loop, more
+// than one level): the last cycle's final sweep also accumulates e . q[dq_par] into scal[8].
+int inner_solve(PlanImpl* P, cudaStream_t s, int dq_par = -1) {
   Level& L0 = P->lv[0];
   Fine F{L0.r, L0.e, &L0.m_res, &L0.m_jac};
   int rc;
-  for (int c = 0; c < P->o.inner_cycles; ++c)
-    if ((rc = vcycle_impl(P, F, c == 0, s))) return rc;
+  for (int c = 0; c < P->o.inner_cycles; ++c) {
+    Fine Fc = F;
+    if (dq_par >= 0 && c + 1 == P->o.inner_cycles) {
+      Fc.jac_maps = &L0.m_jac_dq[dq_par];
+      Fc.dq = P->qi[dq_par];
+      Fc.dq_out = P->scal + 8;
+    }
+    if ((rc = vcycle_impl(P, Fc, c == 0, s))) return rc;
+  }
   return NN4_OK;
 }
+
+// The fused dot applies when the cycle ends in a level-0 Jacobi sweep (more than one level).
+bool fused_dot(const PlanImpl* P) { return P->lv.size() > 1; }
 
 int outer_residual(PlanImpl* P, cudaStream_t s, double* norm2) {
   // r64 = b - A x (FP64) and its squared norm
@@ -654,12 +672,14 @@ int inner_krylov(PlanImpl* P, cudaStream_t s) {
   if (P->T == NN4_BF16 &&
       (rc = K(P, "pointwise:convert", s, [&] { return launch_convert(NN4_F32, P->ri, P->g32, NN4_BF16, L0.r, L0.g, s); })))
     return rc;
+  const bool fuse = fused_dot(P);
   for (int j = 0; j < P->o.inner_krylov; ++j) {
     const int par = j & 1, old = 1 - par;
-    if ((rc = inner_solve(P, s))) return rc;
     if ((rc = check_cuda(cudaMemsetAsync(P->scal + 8, 0, sizeof(double), s), "zero zq"))) return rc;
-    if ((rc = K(P, "inner:dot", s,
-                [&] { return launch_dot(P->T, L0.e, L0.g, NN4_F32, P->qi[old], P->g32, P->scal + 8, s); })))
+    if ((rc = inner_solve(P, s, fuse ? old : -1))) return rc;
+    if (!fuse && (rc = K(P, "inner:dot", s, [&] {
+                    return launch_dot(P->T, L0.e, L0.g, NN4_F32, P->qi[old], P->g32, P->scal + 8, s);
+                  })))
       return rc;
     if ((rc = K(P, "inner:direction", s, [&] {
            return launch_direction(P->T, L0.e, L0.g, NN4_F32, P->pi[old], P->pi[par], P->g32, P->scal + 8,
@@ -808,6 +828,13 @@ int make_level_maps(PlanImpl* P, int l) {
   PassArgs ar = level_args(P, l, L.r, L.t);
   if (!make_pass_maps(&L.m_jac, P->T, aj, L.cfg, L.t, k) || !make_pass_maps(&L.m_res, P->T, ar, L.cfg, L.e, k))
     return set_error(NN4_ECUDA, "tensor map encode failed");
+  if (l == 0 && P->o.inner_krylov > 0)
+    for (int t = 0; t < 2; ++t) {
+      PassArgs ad = aj;
+      ad.dq = P->qi[t];
+      ad.dq_pitch = P->g32.pitch;
+      if (!make_pass_maps(&L.m_jac_dq[t], P->T, ad, L.cfg, L.t, k)) return set_error(NN4_ECUDA, "tensor map encode failed");
+    }
   return NN4_OK;
 }
 

@@ -49,10 +49,12 @@ struct Runner {
   }
 };
 
+// v is returned already added to `base` (the running partial of the same output), so the class
+// sum and the running sum fold into FMAs.
 template <typename T, typename A, int RY, bool PROD, bool ISO>
 __device__ __forceinline__ void plane_uv(const T* __restrict__ sx, const T* __restrict__ sk,
                                          const int* rowoff, int cc, int cl, int cr, const A* c,
-                                         A* u, A* v, A* centre) {
+                                         const A* base, A* u, A* v, A* centre) {
   // Row sums r0 (centre) and r1 (x-neighbours) for the RY+2 rows the thread touches.
   A r0[RY + 2], r1[RY + 2];
 #pragma unroll
@@ -71,10 +73,10 @@ __device__ __forceinline__ void plane_uv(const T* __restrict__ sx, const T* __re
     const A p00 = r0[r + 1], p10 = r1[r + 1];
     const A p01 = r0[r] + r0[r + 2], p11 = r1[r] + r1[r + 2];
     if (ISO) {  // equal spacings: the face classes c[1], c[2], c[4] vanish
-      v[r] = c[0] * p00 + c[3] * p11;
+      v[r] = fma(c[0], p00, fma(c[3], p11, base[r]));
       u[r] = c[5] * p10 + c[6] * p01 + c[7] * p11;
     } else {
-      v[r] = c[0] * p00 + c[1] * p10 + c[2] * p01 + c[3] * p11;
+      v[r] = fma(c[0], p00, fma(c[1], p10, fma(c[2], p01, fma(c[3], p11, base[r]))));
       u[r] = c[4] * p00 + c[5] * p10 + c[6] * p01 + c[7] * p11;
     }
     if (centre) centre[r] = p00;
@@ -87,7 +89,7 @@ __device__ __forceinline__ void plane_uv(const T* __restrict__ sx, const T* __re
 // pointwise tiles (b, L k, 1/diag) of output plane p - 1, all brought by TMA onto one mbarrier,
 // so no global load sits on the critical path of a plane.
 struct Maps {
-  CUtensorMap x, k, b, lk, invd;
+  CUtensorMap x, k, b, lk, invd, dq;
 };
 
 template <typename T, int OP, int VC, bool ISO, int WX, int RY, int TYT, int S>
@@ -99,7 +101,8 @@ struct PassLayout {
   static constexpr int HALO_PAD = ((TX + 2 * AL) * (TY + 2) * (int)sizeof(T) + 127) / 128 * 128;
   static constexpr int PT_PAD = (TX * TY * (int)sizeof(T) + 127) / 128 * 128;
   static constexpr int NP = (HAS_B ? 1 : 0) + (VC == 2 ? 2 : 0);
-  static constexpr int STAGE = NF * HALO_PAD + NP * PT_PAD;
+  static constexpr int DQ_PAD = OP == OP_JACOBI ? (TX * TY * 4 + 127) / 128 * 128 : 0;  // FP32 dq tile
+  static constexpr int STAGE = NF * HALO_PAD + NP * PT_PAD + DQ_PAD;
   static constexpr size_t SMEM = (size_t)S * STAGE + S * 8 + 32 * 8;
 };
 
@@ -122,7 +125,9 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
   constexpr int PT_BYTES = TX * TY * (int)sizeof(T);
   constexpr int PT_PAD = (PT_BYTES + 127) / 128 * 128;
   constexpr int NP = (HAS_B ? 1 : 0) + (VC == 2 ? 2 : 0);  // pointwise slots per stage
-  constexpr int STAGE = NF * HALO_PAD + NP * PT_PAD;
+  constexpr int DQ_BYTES = TX * TY * 4;
+  constexpr int DQ_PAD = OP == OP_JACOBI ? (DQ_BYTES + 127) / 128 * 128 : 0;
+  constexpr int STAGE = NF * HALO_PAD + NP * PT_PAD + DQ_PAD;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * STAGE);
   double* red = reinterpret_cast<double*>(bars + S);
@@ -136,6 +141,7 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
   const int tid = threadIdx.x + TX * threadIdx.y;
   const int nplanes = ze - zs + 2;  // input planes zs-1 .. ze
   const bool use_invd = VC == 2 && OP == OP_JACOBI && a.invd != nullptr;
+  const bool use_dq = OP == OP_JACOBI && a.dq != nullptr;
   const int pt_loads = (HAS_B ? 1 : 0) + (VC == 2 ? 1 : 0) + (use_invd ? 1 : 0);
 
   if (tid == 0) {
@@ -150,7 +156,7 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
     const int zp = mirror(zs - 1 + q, nz);
     const int kout = zs + q - 2;
     const bool pt = q >= 2;
-    mbar_expect_tx(&bars[s], NF * HALO_BYTES + (pt ? pt_loads * PT_BYTES : 0));
+    mbar_expect_tx(&bars[s], NF * HALO_BYTES + (pt ? pt_loads * PT_BYTES + (use_dq ? DQ_BYTES : 0) : 0));
     tma_load_3d(st, &maps.x, x0 - AL, y0 - 1, zp, &bars[s]);
     if (VC) tma_load_3d(st + HALO_PAD, &maps.k, x0 - AL, y0 - 1, zp, &bars[s]);
     if (pt) {
@@ -163,6 +169,7 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
         tma_load_3d(pp, &maps.lk, x0, y0, kout, &bars[s]);
         if (use_invd) tma_load_3d(pp + PT_PAD, &maps.invd, x0, y0, kout, &bars[s]);
       }
+      if (use_dq) tma_load_3d(st + NF * HALO_PAD + NP * PT_PAD, &maps.dq, x0, y0, kout, &bars[s]);
     }
   };
   if (tid == 0) {
@@ -207,7 +214,7 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
   A xc1[RY], kc1[RY];  // centre values of the previous input plane (the pending output)
   // norm and dot partial sums in the compute type for the whole z-march (FP32 for FP32 and BF16
   // storage: the FP64 pipe of this part is narrow), FP64 across threads
-  A nrm = A(0), dt2 = A(0);
+  A nrm = A(0), dt2 = A(0), dqs = A(0);
   const A omega = opaque((A)a.omega);
   bool failed = false;
   T* out = reinterpret_cast<T*>(a.out);
@@ -221,11 +228,12 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
     const T* tb_ = reinterpret_cast<const T*>(st + NF * HALO_PAD);
     const T* tl_ = reinterpret_cast<const T*>(st + NF * HALO_PAD + (HAS_B ? PT_PAD : 0));
     const T* ti_ = tl_ + PT_PAD / sizeof(T);
+    const float* tq_ = reinterpret_cast<const float*>(st + NF * HALO_PAD + NP * PT_PAD);
     A ux[RY], vx[RY], xcn[RY];
-    plane_uv<T, A, RY, false, ISO>(tx_, tx_, rowoff, cc, cl, cr, c, ux, vx, xcn);
+    plane_uv<T, A, RY, false, ISO>(tx_, tx_, rowoff, cc, cl, cr, c, sx.p2, ux, vx, xcn);
     A ukx[RY], vkx[RY], uk[RY], vk[RY], kcn[RY];
-    if (VC) plane_uv<T, A, RY, true, ISO>(tx_, tk_, rowoff, cc, cl, cr, c, ukx, vkx, nullptr);
-    if (VC == 1) plane_uv<T, A, RY, false, ISO>(tk_, tk_, rowoff, cc, cl, cr, c, uk, vk, kcn);
+    if (VC) plane_uv<T, A, RY, true, ISO>(tx_, tk_, rowoff, cc, cl, cr, c, skx.p2, ukx, vkx, nullptr);
+    if (VC == 1) plane_uv<T, A, RY, false, ISO>(tk_, tk_, rowoff, cc, cl, cr, c, sk.p2, uk, vk, kcn);
     if (VC == 2) {
 #pragma unroll
       for (int r = 0; r < RY; ++r) kcn[r] = to_acc(tk_[rowoff[r + 1] + cc]);
@@ -282,7 +290,9 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
               else
                 corr = (bv - Ax) / D;
               const A xn = dirn ? xc1[r] : xc1[r] + omega * corr;
-              out[idx] = from_acc<T>(xn);
+              const T xs = from_acc<T>(xn);
+              out[idx] = xs;
+              if (use_dq) dqs += to_acc(xs) * (A)tq_[po];
             }
           }
         }
@@ -293,16 +303,16 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
       // shift the running sums: the output of this plane still needs u of the next plane
-      sx.p1[r] = sx.p2[r] + vx[r];
+      sx.p1[r] = vx[r];
       sx.p2[r] = ux[r];
       xc1[r] = xcn[r];
       if (VC) {
-        skx.p1[r] = skx.p2[r] + vkx[r];
+        skx.p1[r] = vkx[r];
         skx.p2[r] = ukx[r];
         kc1[r] = kcn[r];
       }
       if (VC == 1) {
-        sk.p1[r] = sk.p2[r] + vk[r];
+        sk.p1[r] = vk[r];
         sk.p2[r] = uk[r];
       }
     }
@@ -324,6 +334,7 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
   }
   if ((OP == OP_RESIDUAL || OP == OP_MATVEC) && a.norm2 != nullptr) block_sum_atomic((double)nrm, a.norm2, red);
   if (OP == OP_MATVEC && a.dot2 != nullptr) block_sum_atomic((double)dt2, a.dot2, red);
+  if (use_dq) block_sum_atomic((double)dqs, a.dq_out, red);
   __syncthreads();  // stage buffers are free for the next tile
   return true;
 }
@@ -527,6 +538,7 @@ bool make_pass_maps(PassMaps* m, nn4_dtype dt, const PassArgs& a, const PassCfg&
   if (a.b) ok = ok && make_tmap_3d(&m->b, dt, a.b, g.nx, g.ny, g.nz, g.pitch, px, py);
   if (a.lk) ok = ok && make_tmap_3d(&m->lk, dt, a.lk, g.nx, g.ny, g.nz, g.pitch, px, py);
   if (a.invd) ok = ok && make_tmap_3d(&m->invd, dt, a.invd, g.nx, g.ny, g.nz, g.pitch, px, py);
+  if (a.dq) ok = ok && make_tmap_3d(&m->dq, NN4_F32, a.dq, g.nx, g.ny, g.nz, a.dq_pitch, px, py);
   return ok;
 }
 
@@ -544,6 +556,8 @@ int launch_pass(nn4_dtype dt, int op, const PassArgs& a, const void* x, const vo
   m.b = a.b ? pm->b : pm->x;
   m.lk = a.lk ? pm->lk : pm->x;
   m.invd = a.invd ? pm->invd : pm->x;
+  m.dq = a.dq ? pm->dq : pm->x;
+  if (a.dq && (op != OP_JACOBI || !a.dq_out)) return set_error(NN4_EINVAL, "the fused dot needs OP_JACOBI and an output");
   if (op != OP_APPLY && !a.b) return set_error(NN4_EINVAL, "stencil pass needs b");
   const int vmode = vc ? (a.lk ? 2 : 1) : 0;
   switch (dt) {
