@@ -151,7 +151,7 @@ def config_dict(args):
                         "1000:1 seeded sphere R=0.2 smoothed over 2 cells, zero-derivative walls, "
                         "f ~ N(0,1) zero-mean, x0 = 0, to 1e-8 relative residual",
             "inner": args.inner, "outer": "flexible CG (FP64)", "inner_cycles": args.m,
-            "inner_krylov": args.krylov,
+            "inner_krylov": args.krylov, "check_every": args.check_every,
             "coarse_operators": "Galerkin", "smoother": "weighted Jacobi omega=2/3, 1 sweep per level",
             "l2": "inputs larger than L2 (b, x, k: 3 x 144 MB FP64 plus the hierarchy)"}
 
@@ -159,15 +159,15 @@ def config_dict(args):
 # ---------------------------------------------------------------- ncu summaries
 # ncu kernel names (template arguments spelled plainly) -> the bench's kernel names.  Several
 # levels share a kernel; the group (same name and grid) with the most time is the finest level.
-NCU_NAMES = [
-    (r"k_pass<double, 3,", "pass64:matvec"), (r"k_pass<double, 1,", "pass64:residual"),
-    (r"k_pass<__nv_bfloat16, 2, 2,", "pass:jacobi:L0"), (r"k_pass<float, 3,", "inner:matvec"),
-    (r"k_fcg_update<float, __nv_bfloat16>", "inner:update"),
-    (r"k_new_direction<__nv_bfloat16, float>", "inner:direction"),
-    (r"k_dot_zq<__nv_bfloat16, float>", "inner:dot"), (r"k_restrict<__nv_bfloat16>", "restrict:L0"),
-    (r"k_prolong<__nv_bfloat16>", "prolong:L0"), (r"k_pass27<__nv_bfloat16, 2>", "pass27:jacobi:L1"),
-    (r"k_coarse<__nv_bfloat16>", "coarse_levels"),
-]
+def ncu_names(tn):
+    """(ncu name prefix, bench kernel name) for an inner storage type spelled `tn` by ncu."""
+    return [
+        (r"k_pass<double, 3,", "pass64:matvec"), (r"k_pass<double, 1,", "pass64:residual"),
+        (f"k_pass<{tn}, 2, 2,", "pass:jacobi:L0"), (r"k_pass<float, 3,", "inner:matvec"),
+        (f"k_fcg_update<float, {tn}>", "inner:update"), (f"k_new_direction<{tn}, float>", "inner:direction"),
+        (f"k_restrict<{tn}>", "restrict:L0"), (f"k_prolong<{tn}>", "prolong:L0"),
+        (f"k_pass27<{tn}, 2>", "pass27:jacobi:L1"), (f"k_coarse<{tn}>", "coarse_levels"),
+    ]
 
 
 def ncu_summary(path, write_traffic):
@@ -204,7 +204,8 @@ def ncu_summary(path, write_traffic):
     if not write_traffic:
         return
     out = {}
-    for pat, bname in NCU_NAMES:
+    tn = "__nv_bfloat16" if any("__nv_bfloat16" in b for b, _ in groups) else "float"
+    for pat, bname in ncu_names(tn):
         cands = [(g["us"], g) for (base, grid), g in groups.items() if base.startswith(pat)]
         if not cands or max(c[1]["dram"] for c in cands) <= 0:
             continue
@@ -215,7 +216,7 @@ def ncu_summary(path, write_traffic):
         out[bname] = {"dram_bytes_per_launch": g["dram"] / g["n"], "launches": g["n"], "source": src,
                       "source_sha256": sha}
     with open(os.path.join(ROOT, "profiles", "ncu_traffic.json"), "w") as f:
-        json.dump(out, f, indent=1, sort_keys=True)
+        json.dump({"inner": "bf16" if tn == "__nv_bfloat16" else "f32", "kernels": out}, f, indent=1, sort_keys=True)
         f.write("\n")
 
 
@@ -225,9 +226,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--inner", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--inner", default="f32", choices=["bf16", "f32"])
     ap.add_argument("--m", type=int, default=1, help="V-cycles per outer iteration (or per inner iteration)")
     ap.add_argument("--krylov", type=int, default=10, help="inner FP32 flexible-CG iterations (0: none)")
+    ap.add_argument("--check-every", type=int, default=1, help="read the residual norm every this many outer iterations")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--ref-n", type=int, default=65)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
@@ -268,7 +270,7 @@ def main():
     B = nn4.to_field(b_host, G)
     X = nn4.field(G)
     inner = nn4.BF16 if args.inner == "bf16" else nn4.F32
-    plan = nn4.Plan(G, K, inner=inner, inner_cycles=args.m, outer=nn4.OUTER_FCG, check_every=2,
+    plan = nn4.Plan(G, K, inner=inner, inner_cycles=args.m, outer=nn4.OUTER_FCG, check_every=args.check_every,
                     inner_krylov=args.krylov)
     stream = torch.cuda.current_stream()
 
@@ -304,13 +306,14 @@ def main():
     value = world * args.steps / (ms / 1000.0)
     if args.only_mixed:
         if rank == 0:
-            print(json.dumps({"n": n, "ms_per_solve": ms_per, "iterations": iters, "kernels": kernels}))
+            print(json.dumps({"n": n, "ms_per_solve": ms_per, "iterations": iters, "kernels": kernels,
+                              "history": info.get("history")}))
         return
     rel_res = info["rel_res"]
     x_mixed = nn4.nodes(X, G).clone()
 
     # plain FP64 GPU path on the same system
-    plan64 = nn4.Plan(G, K, inner=nn4.F64, inner_cycles=1, outer=nn4.OUTER_FCG, check_every=2)
+    plan64 = nn4.Plan(G, K, inner=nn4.F64, inner_cycles=1, outer=nn4.OUTER_FCG, check_every=args.check_every)
     X64 = nn4.field(G)
     solve(plan64, X64)
     barrier()
@@ -357,7 +360,7 @@ def main():
     nbytes = n ** 3 * 8
 
     # per-kernel durations from an eagerly launched, event-timed solve of the same plan setup
-    prof_plan = nn4.Plan(G, K, inner=inner, inner_cycles=args.m, outer=nn4.OUTER_FCG, check_every=2,
+    prof_plan = nn4.Plan(G, K, inner=inner, inner_cycles=args.m, outer=nn4.OUTER_FCG, check_every=args.check_every,
                          profile=True, inner_krylov=args.krylov)
     solve(prof_plan, X)
     prof_plan.profile()
@@ -366,9 +369,10 @@ def main():
     total_prof = sum(v[1] for v in prof.values())
     top = max(prof.items(), key=lambda kv: kv[1][1])
     roof = roofline_entry(top, n, MEASURED.get("fp64_tflops", 1.20), MEASURED.get("hbm_gbs", 6674.5))
-    roof_all = [roofline_entry(kv, n, MEASURED.get("fp64_tflops", 1.20), MEASURED.get("hbm_gbs", 6674.5))
+    sbytes = 2 if args.inner == "bf16" else 4
+    roof_all = [roofline_entry(kv, n, MEASURED.get("fp64_tflops", 1.20), MEASURED.get("hbm_gbs", 6674.5), sbytes)
                 for kv in sorted(prof.items(), key=lambda kv: -kv[1][1])
-                if kv[0] in FLOPS_PER_NODE or (kv[0] in BYTES_PER_NODE and args.inner == "bf16")]
+                if kv[0] in FLOPS_PER_NODE or bytes_per_node(kv[0], sbytes) is not None]
     for r in roof_all:
         r["share"] = round(prof[r["kernel"]][1] / total_prof, 4)
 
@@ -508,16 +512,22 @@ MEASURED = _load_peaks()
 #  -> 44.5 flops; the residual form 43.5 (b - A x, its square).  An FMA counts 2.
 #  Streaming kernels: bytes read + written per node of their level.
 FLOPS_PER_NODE = {"pass64:matvec": 44.5, "pass64:residual": 43.5}
-BYTES_PER_NODE = {
-    "pass:jacobi:L0": 10.0,    # BF16: x (haloed), k, b, L k read; e written
-    "inner:matvec": 20.0,      # FP32: p (haloed), k, L k, r read; q written
-    "inner:update": 26.0,      # FP32 x, r, p, q read; x, r written; BF16 copy of r written
-    "inner:direction": 10.0,   # BF16 z and FP32 p_old read; FP32 p written
-    "inner:dot": 6.0,          # BF16 z and FP32 q read
-    "restrict:L0": 2.25,       # per fine node: BF16 fine read, 1/8 coarse written
-    "prolong:L0": 2.25,        # per fine node: BF16 fine written, 1/8 coarse read
-    "pass27:jacobi:L1": 60.0,  # per L1 node: 27 BF16 coefficients, x (haloed), b read, e written
-}
+
+
+def bytes_per_node(name, s):
+    """Bytes read + written per node of the kernel's level, inner storage of s bytes a value."""
+    table = {
+        "pass:jacobi:L0": 5 * s + 4,   # x (haloed), k, b, L k read; e written; FP32 q_old (fused dot)
+        "inner:matvec": 20.0,          # FP32: p (haloed), k, L k, r read; q written
+        "inner:update": 24.0 + (s if s == 2 else 0),  # FP32 x, r, p, q read; x, r written (+ BF16 copy of r)
+        "inner:direction": s + 8.0,    # z read (storage type), FP32 p_old read, FP32 p written
+        "restrict:L0": 1.125 * s,      # per fine node: fine read, 1/8 coarse written
+        "prolong:L0": 1.125 * s,       # per fine node: fine written, 1/8 coarse read
+        "pass27:jacobi:L1": 30.0 * s,  # per level-1 node: 27 coefficients, x (haloed), b read, e written
+    }
+    return table.get(name)
+
+
 LEVEL = {"pass27:jacobi:L1": 1}  # kernels that run on level 1 ((n+1)/2 nodes per axis)
 KERNEL_SOURCE = {"pass64:matvec": "stencil.cu", "pass64:residual": "stencil.cu", "pass:jacobi:L0": "stencil.cu",
                  "inner:matvec": "stencil.cu", "inner:update": "outer.cu", "inner:direction": "outer.cu",
@@ -525,14 +535,18 @@ KERNEL_SOURCE = {"pass64:matvec": "stencil.cu", "pass64:residual": "stencil.cu",
                  "pass27:jacobi:L1": "galerkin.cu", "coarse_levels": "tail.cu"}
 
 
-def _traffic(name):
+def _traffic(name, inner):
     """DRAM bytes per launch from the committed ncu summary, or None when the kernel's source has
-    changed since the capture (the file hash is recorded with it)."""
+    changed since the capture (the file hash is recorded with it) or the capture ran another inner
+    storage type."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
-            rec = json.load(f).get(name)
+            data = json.load(f)
     except (OSError, ValueError):
         return None
+    if data.get("inner") != inner:
+        return None
+    rec = data.get("kernels", {}).get(name)
     src = KERNEL_SOURCE.get(name)
     if not rec or not src:
         return None
@@ -543,21 +557,22 @@ def _traffic(name):
     return rec.get("dram_bytes_per_launch")
 
 
-def roofline_entry(item, n, fp64_tflops, hbm_gbs):
+def roofline_entry(item, n, fp64_tflops, hbm_gbs, s=4):
     name, (launches, total_ms) = item
     avg_ms = total_ms / max(1, launches)
     nodes = float((n + 1) // 2 if LEVEL.get(name) == 1 else n) ** 3
     if name in FLOPS_PER_NODE:
         achieved = FLOPS_PER_NODE[name] * nodes / (avg_ms * 1e-3) / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
-                "frac": achieved / fp64_tflops, "traffic": _traffic(name), "avg_ms": avg_ms,
+                "frac": achieved / fp64_tflops, "traffic": _traffic(name, "bf16" if s == 2 else "f32"), "avg_ms": avg_ms,
                 "algorithmic": f"{FLOPS_PER_NODE[name]} FP64 flops x {int(nodes)} nodes",
                 "peak_note": "FP64 FMA pipe of this GB300, measured 1.20 TFLOP/s (DFMA loop)"}
-    if name in BYTES_PER_NODE:
-        gbs = BYTES_PER_NODE[name] * nodes / (avg_ms * 1e-3) / 1e9
+    bpn = bytes_per_node(name, s)
+    if bpn is not None:
+        gbs = bpn * nodes / (avg_ms * 1e-3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
-                "frac": gbs / hbm_gbs, "traffic": _traffic(name), "avg_ms": avg_ms,
-                "algorithmic": f"{BYTES_PER_NODE[name]} B x {int(nodes)} nodes",
+                "frac": gbs / hbm_gbs, "traffic": _traffic(name, "bf16" if s == 2 else "f32"), "avg_ms": avg_ms,
+                "algorithmic": f"{bpn} B x {int(nodes)} nodes",
                 "peak_note": "of measured copy bandwidth (MEASURED_PEAKS hbm_gbs)"}
     return {"kernel": name, "bound": None, "avg_ms": avg_ms}
 

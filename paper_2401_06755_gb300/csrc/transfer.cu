@@ -41,47 +41,48 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_restrict(const T* __restrict__ rf, T* __restrict__ rc, const LevelGeom gf,
                                                   const LevelGeom gc) {
   using A = typename Acc<T>::type;
-  const int lane = threadIdx.x;
-  const int I = blockIdx.x * 32 + lane;
+  const int I = blockIdx.x * 32 + threadIdx.x;
   const int J = blockIdx.y * 4 + threadIdx.y;
-  if (J >= gc.ny) return;  // whole warps only: the shuffles below need every lane
+  if (J >= gc.ny) return;
+  // Neighbours that do not exist (past a boundary node) are read at a clamped position with weight
+  // 0, so no load sits behind a branch: the 30 loads of a thread are in flight together.
   const int i0 = 2 * min(I, gc.nx - 1);
   const bool has_r = i0 + 1 < gf.nx;
-  // x-weighted sum of fine row (j, k) at column I
-  // every lane loads its own left neighbour (same cache lines as the pairs): no lane-dependent
-  // branch, so the loads of all rows and planes are in flight together
-  const int il = i0 > 0 ? i0 - 1 : 0;
-  const A wl = i0 > 0 ? A(0.5) : A(0), wr = has_r ? A(0.5) : A(0);
-  auto xsum = [&](long long rowoff) -> A {
-    const T* row = rf + rowoff;
+  const int dl = i0 > 0 ? -1 : 0;
+  const A wl = i0 > 0 ? A(0.5) : A(0), wr = A(0.5);
+  const long long rs = gf.pitch, ps = gf.pitch * (long long)gf.ny;
+  const int j0 = 2 * J;
+  const long long om = J > 0 ? -rs : 0, op = j0 + 1 < gf.ny ? rs : 0;
+  const A wm = J > 0 ? A(0.5) : A(0), wp = j0 + 1 < gf.ny ? A(0.5) : A(0);
+  auto xsum = [&](const T* p) -> A {  // x-weighted sum of a fine row at column I
     A c, r;
-    ld2(row + i0, c, r);
-    const A l = to_acc(row[il]);
+    ld2(p, c, r);  // r lies past the row end for the last column: not used (selected away)
+    const A l = to_acc(p[dl]);
     return c + wl * l + (has_r ? wr * r : A(0));
   };
-  const int j0 = 2 * J;
-  const bool has_jm = J > 0, has_jp = j0 + 1 < gf.ny;
-  auto psum = [&](int k) -> A {  // fine plane k, weighted over rows 2J-1, 2J, 2J+1
-    const long long pk = (long long)gf.ny * k;
-    A v = xsum(gf.pitch * (pk + j0));
-    A side = A(0);
-    if (has_jm) side += xsum(gf.pitch * (pk + j0 - 1));
-    if (has_jp) side += xsum(gf.pitch * (pk + j0 + 1));
-    return v + A(0.5) * side;
-  };
-  const int K0 = blockIdx.z * kRz, K1 = min(gc.nz, K0 + kRz);
-  A prev = K0 > 0 ? psum(2 * K0 - 1) : A(0);
+  auto psum = [&](const T* p) -> A { return xsum(p) + wm * xsum(p + om) + wp * xsum(p + op); };
+  const int K0 = blockIdx.z * kRz;
+  const T* P0 = rf + i0 + rs * j0 + ps * (2 * K0);  // fine plane 2 K0, row 2 J
+  // fine planes 2K0-1 .. 2K0+2kRz-1, clamped into the grid (weight 0 outside)
+  A pl[2 * kRz + 1], wpl[2 * kRz + 1];
+#pragma unroll
+  for (int q = 0; q <= 2 * kRz; ++q) {
+    const int k = 2 * K0 - 1 + q;
+    const int kc = min(max(k, 0), gf.nz - 1);
+    wpl[q] = (k >= 0 && k < gf.nz) ? A(1) : A(0);
+    pl[q] = psum(P0 + ps * (kc - 2 * K0));
+  }
   const bool dxy = (gc.dir[0] && I == 0) || (gc.dir[1] && I == gc.nx - 1) || (gc.dir[2] && J == 0) ||
                    (gc.dir[3] && J == gc.ny - 1);
+  T* out = rc + I + gc.pitch * ((long long)J + (long long)gc.ny * K0);
+  const long long cps = gc.pitch * (long long)gc.ny;
 #pragma unroll
-  for (int K = K0; K < K0 + kRz; ++K) {
-    if (K >= K1) break;
-    const A p0 = psum(2 * K);
-    const A p1 = 2 * K + 1 < gf.nz ? psum(2 * K + 1) : A(0);
-    const A v = p0 + A(0.5) * (prev + p1);
-    prev = p1;
+  for (int t = 0; t < kRz; ++t) {
+    const int K = K0 + t;
+    if (K >= gc.nz) break;
+    const A v = pl[2 * t + 1] + A(0.5) * (wpl[2 * t] * pl[2 * t] + wpl[2 * t + 2] * pl[2 * t + 2]);
     const bool dn = dxy || (gc.dir[4] && K == 0) || (gc.dir[5] && K == gc.nz - 1);
-    if (I < gc.nx) rc[I + gc.pitch * ((long long)J + (long long)gc.ny * K)] = from_acc<T>(dn ? A(0) : v);
+    if (I < gc.nx) out[cps * t] = from_acc<T>(dn ? A(0) : v);
   }
 }
 
@@ -105,10 +106,11 @@ __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ ec, T* ef
   // (x-even, x-odd) values of coarse plane K at fine row j
   // rows J0 and J1 (= J0 for an even j, weight 1/2 each then): the branch-free sum of both
   const int In = has_next ? Ic + 1 : Ic;
+  const T* const c0 = ec + gc.pitch * (long long)J0;
+  const long long d1 = gc.pitch * (long long)(J1 - J0), cps = gc.pitch * (long long)gc.ny;
   auto plane = [&](int K, A& ve, A& vo) {
-    const T* p = ec + gc.pitch * (long long)gc.ny * K;
-    const T* r0 = p + gc.pitch * (long long)J0;
-    const T* r1 = p + gc.pitch * (long long)J1;
+    const T* r0 = c0 + cps * K;
+    const T* r1 = r0 + d1;
     const A a = A(0.5) * (to_acc(r0[Ic]) + to_acc(r1[Ic]));
     const A an = A(0.5) * (to_acc(r0[In]) + to_acc(r1[In]));
     ve = a;
@@ -130,6 +132,8 @@ __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ ec, T* ef
   const bool dy = (gf.dir[2] && j == 0) || (gf.dir[3] && j == gf.ny - 1);
   const bool d0x = (gf.dir[0] && i == 0) || (gf.dir[1] && i == gf.nx - 1);
   const bool d1x = gf.dir[1] && i + 1 == gf.nx - 1;
+  T* const out0 = ef + i + gf.pitch * ((long long)j + (long long)gf.ny * k0);
+  const long long fps = gf.pitch * (long long)gf.ny;
 #pragma unroll
   for (int t = 0; t < kPz; ++t) {
     const int k = k0 + t;
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ ec, T* ef
     A v0 = (t & 1) ? A(0.5) * (ce[t >> 1] + ce[(t >> 1) + 1]) : ce[t >> 1];
     A v1 = (t & 1) ? A(0.5) * (co[t >> 1] + co[(t >> 1) + 1]) : co[t >> 1];
     const bool dz = dy || (gf.dir[4] && k == 0) || (gf.dir[5] && k == gf.nz - 1);
-    T* out = ef + i + gf.pitch * ((long long)j + (long long)gf.ny * k);
+    T* out = out0 + fps * t;
     A b0 = A(0), b1 = A(0);
     if (base) {
       const T* bp = base + (out - ef);
