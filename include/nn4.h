@@ -122,11 +122,14 @@ typedef struct {
   int32_t inner_krylov;  /* 0: the preconditioner is inner_cycles V-cycles.  n > 0: it is n
                             iterations of flexible CG in FP32 vectors on A e = r, each
                             preconditioned by inner_cycles V-cycles (mixed precision only) */
-  int32_t coarse_tail;   /* 1: run every level at or below 6000 nodes in one single-CTA launch
-                            (same arithmetic as the per-level kernels); 0: one launch per step */
+  int32_t coarse_tail;   /* 1: run the coarse levels in one launch (see coarse_entry_nodes; same
+                            arithmetic as the per-level kernels); 0: one launch per step */
   int32_t autotune;      /* 1: time the compiled tile shapes, pipeline depths and z-march depths
                             of every stencil pass at plan creation and keep the fastest (cached
                             per process by grid size); 0: fixed defaults */
+  int32_t coarse_entry_nodes; /* with coarse_tail: levels with at most this many nodes (0: 40000)
+                            run in one cooperative launch over all SMs when the first of them has
+                            more than 800 nodes */
 } nn4_plan_opts;
 
 /* Fills o with the defaults: F64, 1 cycle, NN4_OUTER_CYCLES, omega 2/3, graphs on, check 1,

@@ -164,7 +164,7 @@ struct GridBarrier {
   unsigned gen;
 };
 constexpr int kCoarseThreads = 512;
-constexpr long long kCoarseNodes = 300000;
+constexpr long long kCoarseNodes = 40000;
 int launch_coarse(nn4_dtype dt, const TailArgs& a, GridBarrier* bar, cudaStream_t s);
 // One CTA per instance (tab: device array of `count` tails; `active` skips converged ones).
 int launch_tail_batch(nn4_dtype dt, const TailArgs* tab, int count, const int* active, cudaStream_t s);

@@ -178,7 +178,10 @@ __global__ void k_dot_zq(const TZ* __restrict__ z, LevelGeom gz, const V* __rest
 template <typename TZ, typename V>
 __global__ void k_new_direction(const TZ* __restrict__ z, LevelGeom gz, const V* __restrict__ p_old,
                                 V* __restrict__ p, LevelGeom gv, const double* zq, const double* pq_old) {
-  const V beta = (V)(*zq / *pq_old);
+  __shared__ V beta_s;
+  if (threadIdx.x == 0 && threadIdx.y == 0) beta_s = (V)(*zq / *pq_old);  // one FP64 division per block
+  __syncthreads();
+  const V beta = beta_s;
   NN4_FOR_CHUNKS(gv) {
     const TZ* zp = z + row * gz.pitch + i0;
     const long long o = row * gv.pitch + i0;
@@ -198,7 +201,10 @@ __global__ void k_fcg_update(V* __restrict__ x, V* __restrict__ r, const V* __re
                              const V* __restrict__ q, LevelGeom gv, TR* __restrict__ rT, LevelGeom gT,
                              const double* pr, const double* pq, double* norm2) {
   __shared__ double red[32];
-  const V alpha = (V)(*pr / *pq);
+  __shared__ V alpha_s;
+  if (threadIdx.x == 0 && threadIdx.y == 0) alpha_s = (V)(*pr / *pq);  // one FP64 division per block
+  __syncthreads();
+  const V alpha = alpha_s;
   V s = 0;
   NN4_FOR_CHUNKS(gv) {
     const long long o = row * gv.pitch + i0;

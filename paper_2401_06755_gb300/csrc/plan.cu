@@ -60,6 +60,8 @@ struct PlanImpl {
          *q64[2] = {nullptr, nullptr}, *k64 = nullptr;
   double *lk64 = nullptr, *invd64 = nullptr;  // L k and 1/diag(A) for Eq. k-T (FP64)
   void* lkT = nullptr;      // L k in the inner storage type at the level-0 pitch
+  void* invdT = nullptr;    // 1/diag(A) in the inner storage type (the level-0 Jacobi sweep multiplies
+                            // by it instead of dividing per node)
   float* lk32 = nullptr;    // L k in FP32 for the inner Krylov mat-vec
   // inner flexible CG in FP32 vectors (opts.inner_krylov > 0): solution y, residual r, directions
   // p[2], q[2], coefficient k (FP32), all at the FP32 level-0 pitch
@@ -505,7 +507,7 @@ PassArgs level_args(PlanImpl* P, int l, const void* b, void* out) {
   a.zchunk = L.cfg.zchunk;
   if (P->vc && l == 0) {
     a.lk = P->lkT;
-    a.invd = P->T == NN4_F64 ? P->invd64 : nullptr;
+    a.invd = P->T == NN4_F64 ? P->invd64 : P->invdT;
   }
   return a;
 }
@@ -1133,6 +1135,7 @@ void nn4_plan_opts_default(nn4_plan_opts* o) {
   o->inner_krylov = 0;
   o->coarse_tail = 1;
   o->autotune = 1;
+  o->coarse_entry_nodes = 0;
 }
 
 int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opts, nn4_plan* out) {
@@ -1187,8 +1190,9 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
     // kTailNodes nodes: the single-CTA tail; more: the cooperative kernel over all SMs.
     auto nodes = [&](int l) { return (long long)P->lv[l].g.nx * P->lv[l].g.ny * P->lv[l].g.nz; };
     int E = -1;
+    const long long entry = o.coarse_entry_nodes > 0 ? o.coarse_entry_nodes : kCoarseNodes;
     for (int l = 1; l < nl; ++l)
-      if (nodes(l) <= kCoarseNodes) {
+      if (nodes(l) <= entry) {
         E = l;
         break;
       }
@@ -1293,7 +1297,9 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
     if (P->T == NN4_F64) {
       P->lkT = P->lk64;
     } else if ((rc = alloc(P, &P->lkT, field_bytes(P->lv[0].g, P->T))) ||
-               (rc = launch_convert(NN4_F64, P->lk64, P->g64, P->T, P->lkT, P->lv[0].g, 0))) {
+               (rc = launch_convert(NN4_F64, P->lk64, P->g64, P->T, P->lkT, P->lv[0].g, 0)) ||
+               (rc = alloc(P, &P->invdT, field_bytes(P->lv[0].g, P->T))) ||
+               (rc = launch_convert(NN4_F64, P->invd64, P->g64, P->T, P->invdT, P->lv[0].g, 0))) {
       destroy(P);
       return rc;
     }

@@ -399,8 +399,11 @@ int launch_t(const PassArgs& a, const Maps& maps, cudaStream_t st) {
 }
 
 // The configurations the autotuner chooses from: {WX, RY, TYT, S}.
-constexpr int kCfgs[][4] = {{1, 4, 4, 3}, {2, 2, 4, 4}, {1, 2, 8, 3}, {2, 4, 2, 4}};
-constexpr int kNumCfgs = 4;
+// The last ({1, 8, 2, 3}: eight rows a thread) is compiled for FP64 only, whose passes are bound by
+// the FP64 pipe and gain from the fewer loads per output; for the other types it is refused and
+// the autotuner skips it.
+constexpr int kCfgs[][4] = {{1, 4, 4, 3}, {2, 2, 4, 4}, {1, 2, 8, 3}, {2, 4, 2, 4}, {1, 8, 2, 3}};
+constexpr int kNumCfgs = 5;
 
 template <typename T, int OP, int VC, bool ISO>
 int dispatch_cfg(const PassArgs& a, const PassCfg& cfg, const Maps& m, cudaStream_t st) {
@@ -411,6 +414,9 @@ int dispatch_cfg(const PassArgs& a, const PassCfg& cfg, const Maps& m, cudaStrea
         case 1: return launch_t<T, OP, VC, ISO, 2, 2, 4, 4>(a, m, st);
         case 2: return launch_t<T, OP, VC, ISO, 1, 2, 8, 3>(a, m, st);
         case 3: return launch_t<T, OP, VC, ISO, 2, 4, 2, 4>(a, m, st);
+        case 4:
+          if constexpr (sizeof(T) == 8) return launch_t<T, OP, VC, ISO, 1, 8, 2, 3>(a, m, st);
+          break;
       }
     }
   return set_error(NN4_EINVAL, "unsupported stencil pass configuration");

@@ -42,7 +42,8 @@ class _PlanOpts(ctypes.Structure):
     _fields_ = [("inner", ctypes.c_int), ("inner_cycles", ctypes.c_int32), ("outer", ctypes.c_int32),
                 ("omega", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32), ("inner_krylov", ctypes.c_int32),
-                ("coarse_tail", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("coarse_tail", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("coarse_entry_nodes", ctypes.c_int32)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -290,7 +291,8 @@ class Plan:
     """Multigrid hierarchy for one grid (and optional FP64 coefficient field k)."""
 
     def __init__(self, grid, k=None, inner=F64, inner_cycles=1, outer=OUTER_CYCLES, omega=2.0 / 3.0,
-                 use_graph=True, check_every=1, profile=False, inner_krylov=0, coarse_tail=True, autotune=True):
+                 use_graph=True, check_every=1, profile=False, inner_krylov=0, coarse_tail=True, autotune=True,
+                 coarse_entry_nodes=0):
         o = _PlanOpts()
         lib().nn4_plan_opts_default(ctypes.byref(o))
         o.inner, o.inner_cycles, o.outer = int(inner), int(inner_cycles), int(outer)
@@ -299,6 +301,7 @@ class Plan:
         o.inner_krylov = int(inner_krylov)
         o.coarse_tail = int(bool(coarse_tail))
         o.autotune = int(bool(autotune))
+        o.coarse_entry_nodes = int(coarse_entry_nodes)
         self.grid = grid
         self.inner = inner
         self._k = k  # keep the coefficient alive while the plan exists
