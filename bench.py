@@ -517,7 +517,7 @@ FLOPS_PER_NODE = {"pass64:matvec": 44.5, "pass64:residual": 43.5}
 def bytes_per_node(name, s):
     """Bytes read + written per node of the kernel's level, inner storage of s bytes a value."""
     table = {
-        "pass:jacobi:L0": 5 * s + 4,   # x (haloed), k, b, L k read; e written; FP32 q_old (fused dot)
+        "pass:jacobi:L0": 6 * s + 4,   # x (haloed), k, b, L k, 1/diag read; e written; FP32 q_old (fused dot)
         "inner:matvec": 20.0,          # FP32: p (haloed), k, L k, r read; q written
         "inner:update": 24.0 + (s if s == 2 else 0),  # FP32 x, r, p, q read; x, r written (+ BF16 copy of r)
         "inner:direction": s + 8.0,    # z read (storage type), FP32 p_old read, FP32 p written
