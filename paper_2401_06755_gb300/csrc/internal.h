@@ -39,7 +39,7 @@ struct PassArgs {
   double* norm2;     // optional: += sum out^2 (OP_RESIDUAL) or x.out (OP_MATVEC)
   double* dot2;      // OP_MATVEC: += x.b
   int zchunk;        // output planes per block
-  // Eq. k-T with precomputed fields (optional): lk = L k (assembled, pitch g.pitch) replaces the
+  // Eq. k-T with precomputed fields (optional): lk = (1/2) L k (assembled, pitch g.pitch) replaces the
   // on-the-fly stencil of k; invd = 1 / diag(A) replaces the division in Jacobi.
   const void* lk;
   const void* invd;

@@ -228,15 +228,15 @@ __global__ void k_fcg_update(V* __restrict__ x, V* __restrict__ r, const V* __re
   block_sum_atomic((double)s, norm2, red);
 }
 
-// invd = 1 / (w c0 k - L k / 2): the diagonal of Eq. k-T (w = prod_d s_d / 2, c0 the interior
+// invd = 1 / (w c0 k - hlk) with hlk = (1/2) L k: the diagonal of Eq. k-T (w = prod_d s_d / 2, c0 the interior
 // centre weight of the stencil).
-__global__ void k_inv_diag(const double* __restrict__ k, const double* __restrict__ lk, double* __restrict__ invd,
+__global__ void k_inv_diag(const double* __restrict__ k, const double* __restrict__ hlk, double* __restrict__ invd,
                            LevelGeom g, double c0) {
   NN4_FOR_NODES(g) {
     const int j = (int)(row % g.ny), kk = (int)(row / g.ny);
     const double w = 0.125 * ((i > 0) + (i < g.nx - 1)) * ((j > 0) + (j < g.ny - 1)) * ((kk > 0) + (kk < g.nz - 1));
     const long long o = row * g.pitch + i;
-    invd[o] = 1.0 / (w * c0 * k[o] - 0.5 * lk[o]);
+    invd[o] = 1.0 / (w * c0 * k[o] - hlk[o]);
   }
 }
 

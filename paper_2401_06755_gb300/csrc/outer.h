@@ -11,7 +11,7 @@ int launch_add_correction(nn4_dtype dt, double* x, const LevelGeom& g64, const v
 // rT = (inner type) r
 int launch_to_inner(nn4_dtype dt, const double* r, const LevelGeom& g64, void* rT, const LevelGeom& gT,
                     cudaStream_t s);
-// invd = 1 / diag(A) for Eq. k-T from k and lk = L k (FP64)
+// invd = 1 / diag(A) for Eq. k-T from k and lk = (1/2) L k (FP64)
 int launch_inv_diag(const double* k, const double* lk, double* invd, const LevelGeom& g, double c0,
                     cudaStream_t s);
 // r = b at free nodes, 0 at Dirichlet nodes

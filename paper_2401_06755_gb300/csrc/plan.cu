@@ -58,11 +58,11 @@ struct PlanImpl {
   PassCfg cfg64;
   double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr, *p64[2] = {nullptr, nullptr},
          *q64[2] = {nullptr, nullptr}, *k64 = nullptr;
-  double *lk64 = nullptr, *invd64 = nullptr;  // L k and 1/diag(A) for Eq. k-T (FP64)
-  void* lkT = nullptr;      // L k in the inner storage type at the level-0 pitch
+  double *lk64 = nullptr, *invd64 = nullptr;  // (1/2) L k and 1/diag(A) for Eq. k-T (FP64)
+  void* lkT = nullptr;      // (1/2) L k in the inner storage type at the level-0 pitch
   void* invdT = nullptr;    // 1/diag(A) in the inner storage type (the level-0 Jacobi sweep multiplies
                             // by it instead of dividing per node)
-  float* lk32 = nullptr;    // L k in FP32 for the inner Krylov mat-vec
+  float* lk32 = nullptr;    // (1/2) L k in FP32 for the inner Krylov mat-vec
   // inner flexible CG in FP32 vectors (opts.inner_krylov > 0): solution y, residual r, directions
   // p[2], q[2], coefficient k (FP32), all at the FP32 level-0 pitch
   LevelGeom g32;
@@ -1274,10 +1274,12 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
       destroy(P);
       return rc;
     }
-    // L k (assembled, natural faces) and the inverse diagonal, once per plan
+    // (1/2) L k (assembled, natural faces; the operator's coefficients halved, exactly) and the
+    // inverse diagonal, once per plan
     PassArgs a{};
     a.g = P->g64;
     a.L = P->L64;
+    for (int c = 0; c < 8; ++c) a.L.c[c] *= 0.5;
     a.out = P->lk64;
     PassCfg cfg0 = default_pass_cfg(NN4_F64, false, P->g64);
     a.zchunk = cfg0.zchunk;

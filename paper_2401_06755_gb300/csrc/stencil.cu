@@ -83,8 +83,8 @@ __device__ __forceinline__ void plane_uv(const T* __restrict__ sx, const T* __re
   }
 }
 
-// VC: 0 constant coefficient; 1 Eq. k-T with L k on the fly; 2 Eq. k-T with L k (and optionally
-// the inverse diagonal) read pointwise.  The CTA covers TX = 32 WX columns and TY = TYT RY rows.
+// VC: 0 constant coefficient; 1 Eq. k-T with L k on the fly; 2 Eq. k-T with (1/2) L k (and
+// optionally the inverse diagonal) read pointwise.  The CTA covers TX = 32 WX columns and TY = TYT RY rows.
 // Every pipeline stage holds the haloed tiles of input plane p (x, and k for Eq. k-T) and the
 // pointwise tiles (b, L k, 1/diag) of output plane p - 1, all brought by TMA onto one mbarrier,
 // so no global load sits on the critical path of a plane.
@@ -195,12 +195,13 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
 #pragma unroll
   for (int t = 0; t < 8; ++t) c[t] = (A)a.L.c[t];
   const A wx = (A)half_count(ic, nx);
-  A wy[RY];
+  A wy[RY], hwy[RY];  // boundary weight of each row (x and y factors) and half of it
   unsigned dmask = 0;  // bit r: output row r lies on a Dirichlet face of x or y
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
     const int j = min(jb + r, ny - 1);
     wy[r] = wx * (A)half_count(j, ny);
+    hwy[r] = (A)0.5 * wy[r];
     const bool d = (g.dir[0] && i == 0) || (g.dir[1] && i == nx - 1) || (g.dir[2] && j == 0) || (g.dir[3] && j == ny - 1);
     dmask |= (d ? 1u : 0u) << r;
   }
@@ -259,8 +260,8 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
             D = w * (c[0] * kc1[r] - (A)0.5 * Lk);
           } else if (VC == 2) {
             const A Lkx = skx.p1[r] + ukx[r];
-            const A hLk = (A)0.5 * to_acc(tl_[po]);  // 1/2 (L k), w included
-            Ax = (A)0.5 * w * (Lkx + kc1[r] * Lx) - xc1[r] * hLk;
+            const A hLk = to_acc(tl_[po]);  // (1/2) L k as stored, w included
+            Ax = fma(hwy[r] * wz, fma(kc1[r], Lx, Lkx), -xc1[r] * hLk);
             D = w * c[0] * kc1[r] - hLk;
           } else {
             Ax = w * Lx;
