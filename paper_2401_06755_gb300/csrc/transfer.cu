@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(128) k_restrict(const T* __restrict__ rf, T* _
   const int J = blockIdx.y * 4 + threadIdx.y;
   if (J >= gc.ny) return;
   // Neighbours that do not exist (past a boundary node) are read at a clamped position with weight
-  // 0, so no load sits behind a branch: the 30 loads of a thread are in flight together.
+  // 0, so no load sits behind a branch.
   const int i0 = 2 * min(I, gc.nx - 1);
   const bool has_r = i0 + 1 < gf.nx;
   const int dl = i0 > 0 ? -1 : 0;
@@ -54,23 +54,32 @@ __global__ void __launch_bounds__(128) k_restrict(const T* __restrict__ rf, T* _
   const int j0 = 2 * J;
   const long long om = J > 0 ? -rs : 0, op = j0 + 1 < gf.ny ? rs : 0;
   const A wm = J > 0 ? A(0.5) : A(0), wp = j0 + 1 < gf.ny ? A(0.5) : A(0);
-  auto xsum = [&](const T* p) -> A {  // x-weighted sum of a fine row at column I
-    A c, r;
-    ld2(p, c, r);  // r lies past the row end for the last column: not used (selected away)
-    const A l = to_acc(p[dl]);
-    return c + wl * l + (has_r ? wr * r : A(0));
-  };
-  auto psum = [&](const T* p) -> A { return xsum(p) + wm * xsum(p + om) + wp * xsum(p + op); };
   const int K0 = blockIdx.z * kRz;
   const T* P0 = rf + i0 + rs * j0 + ps * (2 * K0);  // fine plane 2 K0, row 2 J
-  // fine planes 2K0-1 .. 2K0+2kRz-1, clamped into the grid (weight 0 outside)
-  A pl[2 * kRz + 1], wpl[2 * kRz + 1];
+  // Every raw value first (fine planes 2K0-1 .. 2K0+2kRz-1, clamped into the grid with weight 0
+  // outside; rows 2J-1, 2J, 2J+1), then the arithmetic: all 2 (2 kRz + 1) 3 loads in flight.
+  constexpr int NPL = 2 * kRz + 1;
+  A c[NPL][3], r[NPL][3], l[NPL][3], wpl[NPL];
 #pragma unroll
-  for (int q = 0; q <= 2 * kRz; ++q) {
+  for (int q = 0; q < NPL; ++q) {
     const int k = 2 * K0 - 1 + q;
     const int kc = min(max(k, 0), gf.nz - 1);
     wpl[q] = (k >= 0 && k < gf.nz) ? A(1) : A(0);
-    pl[q] = psum(P0 + ps * (kc - 2 * K0));
+    const T* pq = P0 + ps * (kc - 2 * K0);
+    const long long ro[3] = {om, 0, op};
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      ld2(pq + ro[w], c[q][w], r[q][w]);  // r lies past the row end for the last column: not used
+      l[q][w] = to_acc(pq[ro[w] + dl]);
+    }
+  }
+  A pl[NPL];
+#pragma unroll
+  for (int q = 0; q < NPL; ++q) {
+    A row[3];
+#pragma unroll
+    for (int w = 0; w < 3; ++w) row[w] = c[q][w] + wl * l[q][w] + (has_r ? wr * r[q][w] : A(0));
+    pl[q] = row[1] + wm * row[0] + wp * row[2];
   }
   const bool dxy = (gc.dir[0] && I == 0) || (gc.dir[1] && I == gc.nx - 1) || (gc.dir[2] && J == 0) ||
                    (gc.dir[3] && J == gc.ny - 1);
@@ -119,14 +128,10 @@ __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ ec, T* ef
   const int k0 = blockIdx.z * kPz, k1 = min(gf.nz, k0 + kPz);
   const int K0 = k0 >> 1;
   A ce[kPz / 2 + 1], co[kPz / 2 + 1];
+  // coarse planes past the grid are clamped (their values only feed fine planes past the grid,
+  // which are not stored), so all coarse loads are issued without a branch
 #pragma unroll
-  for (int t = 0; t <= kPz / 2; ++t) {
-    if (K0 + t < gc.nz) {
-      plane(K0 + t, ce[t], co[t]);
-    } else {
-      ce[t] = co[t] = A(0);
-    }
-  }
+  for (int t = 0; t <= kPz / 2; ++t) plane(min(K0 + t, gc.nz - 1), ce[t], co[t]);
   const int i = 2 * I;
   const bool ok0 = I < gc.nx, ok1 = i + 1 < gf.nx;
   const bool dy = (gf.dir[2] && j == 0) || (gf.dir[3] && j == gf.ny - 1);
