@@ -130,7 +130,15 @@ typedef struct {
   int32_t coarse_entry_nodes; /* with coarse_tail: levels with at most this many nodes (0: 40000)
                             run in one cooperative launch over all SMs when the first of them has
                             more than 800 nodes */
+  int32_t pass_shape;    /* -1: tile shapes autotuned (autotune = 1) or the defaults.  0 ..
+                            nn4_pass_shapes() - 1: that compiled tile shape for every stencil pass
+                            that has it (overrides autotune; shapes compiled for FP64 only leave
+                            the FP32/BF16 passes at their default).  For verification */
 } nn4_plan_opts;
+
+/* Number of compiled stencil-pass tile shapes (the range of nn4_plan_opts.pass_shape).  The
+   paper has no counterpart: tiling is an implementation choice.  Never fails. */
+int32_t nn4_pass_shapes(void);
 
 /* Fills o with the defaults: F64, 1 cycle, NN4_OUTER_CYCLES, omega 2/3, graphs on, check 1,
  * profile off, no inner Krylov loop, coarse tail on, autotuning on. */

@@ -160,16 +160,9 @@ __global__ void k_pass27(const T* __restrict__ x, const T* __restrict__ a27, con
     for (int dy = 0; dy < 3; ++dy)
       row[dy + 3 * dz] = g.pitch * ((long long)mirror(j + dy - 1, g.ny) + (long long)g.ny * mirror(k + dz - 1, g.nz));
   const T* ap = a27 + o;
-  // all 54 loads first, then the products: the loads are in flight together
-  T cv[27], xv[27];
-#pragma unroll
-  for (int d = 0; d < 27; ++d) {
-    cv[d] = ap[d * plane];
-    xv[d] = x[row[d / 3] + ix[d % 3]];
-  }
   A s = 0;
 #pragma unroll
-  for (int d = 0; d < 27; ++d) s += to_acc(cv[d]) * to_acc(xv[d]);
+  for (int d = 0; d < 27; ++d) s += to_acc(ap[d * plane]) * to_acc(x[row[d / 3] + ix[d % 3]]);
   const bool dn = dnode(g, i, j, k);
   const A bv = to_acc(reinterpret_cast<const T*>(a.b)[o]);
   T* out = reinterpret_cast<T*>(a.out);
@@ -177,7 +170,7 @@ __global__ void k_pass27(const T* __restrict__ x, const T* __restrict__ a27, con
     out[o] = from_acc<T>(dn ? A(0) : bv - s);
   } else {
     const A xc = to_acc(x[o]);
-    const A D = to_acc(cv[13]);
+    const A D = to_acc(ap[13 * plane]);
     const A omega = (A)a.omega;
     A corr;
     if constexpr (sizeof(A) == 4)

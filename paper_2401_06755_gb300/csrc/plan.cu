@@ -932,6 +932,19 @@ int tune_pass(nn4_dtype dt, int op, PassArgs a, const void* x, const void* k, Pa
   return NN4_OK;
 }
 
+// Every stencil pass of the plan on compiled shape `index` (z chunks as by default); shapes
+// compiled for FP64 only are applied to the FP64 passes only.
+void force_pass_shape(PlanImpl* P, int index) {
+  const bool fp64_only = index == num_pass_cfgs() - 1;
+  auto apply = [&](PassCfg* c, nn4_dtype dt, const LevelGeom& g) {
+    if (fp64_only && dt != NN4_F64) return;
+    *c = pass_cfg_candidate(index, g, c->zchunk);
+  };
+  for (auto& L : P->lv) apply(&L.cfg, P->T, L.g);
+  apply(&P->cfg64, NN4_F64, P->g64);
+  if (P->o.inner_krylov > 0) apply(&P->cfg32, NN4_F32, P->g32);
+}
+
 int autotune_plan(PlanImpl* P) {
   int rc;
   cudaStream_t s = 0;
@@ -1136,6 +1149,7 @@ void nn4_plan_opts_default(nn4_plan_opts* o) {
   o->coarse_tail = 1;
   o->autotune = 1;
   o->coarse_entry_nodes = 0;
+  o->pass_shape = -1;
 }
 
 int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opts, nn4_plan* out) {
@@ -1318,7 +1332,13 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
       }
     }
   }
-  if (o.autotune && (rc = autotune_plan(P))) {
+  if (o.pass_shape >= num_pass_cfgs()) {
+    destroy(P);
+    return set_error(NN4_EINVAL, "pass_shape out of range");
+  }
+  if (o.pass_shape >= 0) {
+    force_pass_shape(P, o.pass_shape);
+  } else if (o.autotune && (rc = autotune_plan(P))) {
     destroy(P);
     return rc;
   }
@@ -1359,6 +1379,8 @@ int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opt
   *out = h;
   return NN4_OK;
 }
+
+int32_t nn4_pass_shapes(void) { return num_pass_cfgs(); }
 
 int nn4_plan_destroy(nn4_plan p) {
   if (!p) return NN4_OK;

@@ -43,7 +43,7 @@ class _PlanOpts(ctypes.Structure):
                 ("omega", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32), ("inner_krylov", ctypes.c_int32),
                 ("coarse_tail", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("coarse_entry_nodes", ctypes.c_int32)]
+                ("coarse_entry_nodes", ctypes.c_int32), ("pass_shape", ctypes.c_int32)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -133,6 +133,7 @@ def lib():
             "nn4_last_error": (ctypes.c_char_p, []),
             "nn4_device_error": (ctypes.c_int, []),
             "nn4_version": (ctypes.c_char_p, []),
+            "nn4_pass_shapes": (ctypes.c_int32, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -287,12 +288,17 @@ def version():
     return lib().nn4_version().decode()
 
 
+def pass_shapes():
+    """Number of compiled stencil-pass tile shapes (values of Plan(pass_shape=...))."""
+    return int(lib().nn4_pass_shapes())
+
+
 class Plan:
     """Multigrid hierarchy for one grid (and optional FP64 coefficient field k)."""
 
     def __init__(self, grid, k=None, inner=F64, inner_cycles=1, outer=OUTER_CYCLES, omega=2.0 / 3.0,
                  use_graph=True, check_every=1, profile=False, inner_krylov=0, coarse_tail=True, autotune=True,
-                 coarse_entry_nodes=0):
+                 coarse_entry_nodes=0, pass_shape=-1):
         o = _PlanOpts()
         lib().nn4_plan_opts_default(ctypes.byref(o))
         o.inner, o.inner_cycles, o.outer = int(inner), int(inner_cycles), int(outer)
@@ -302,6 +308,7 @@ class Plan:
         o.coarse_tail = int(bool(coarse_tail))
         o.autotune = int(bool(autotune))
         o.coarse_entry_nodes = int(coarse_entry_nodes)
+        o.pass_shape = int(pass_shape)
         self.grid = grid
         self.inner = inner
         self._k = k  # keep the coefficient alive while the plan exists

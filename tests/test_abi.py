@@ -33,6 +33,16 @@ def test_every_declared_symbol_is_exported(nn4):
     assert not missing, missing
 
 
+def test_plan_options_layout_and_shapes(nn4):
+    """The binding's option struct matches the header (the trailing fields get the C defaults)."""
+    o = nn4._PlanOpts()
+    o.coarse_entry_nodes = 123
+    o.pass_shape = 7
+    nn4.lib().nn4_plan_opts_default(ctypes.byref(o))
+    assert o.coarse_entry_nodes == 0 and o.pass_shape == -1 and o.autotune == 1
+    assert nn4.pass_shapes() == 5
+
+
 def test_row_pitch(nn4):
     assert nn4.row_pitch(257, nn4.F64) == 272
     assert nn4.row_pitch(257, nn4.F32) == 288

@@ -83,6 +83,37 @@ def test_vcycle_fp64_per_cycle(ci):
             assert _rel(xg, x) <= 1e-12, f"cycle {c}: {_rel(xg, x):.3e}"
 
 
+@pytest.mark.parametrize("shape", range(5))
+def test_every_tile_shape(shape):
+    """Each compiled tile shape of the stencil pass, forced on every pass of a plan, gives the
+    oracle's FP64 cycle to 1e-12 and a mixed FP32 flexible-CG solve (fused dot, precomputed 1/D)
+    within 1e-8 of the oracle's converged solution.  Eq. k-T with a 1000:1 sphere, Dirichlet on two
+    faces, sizes that leave ragged tiles along every axis; the coarse levels run in the cooperative
+    launch with the dense tail map."""
+    need_gpu()
+    nn4 = _nn4()
+    assert nn4.pass_shapes() == 5
+    bc = (False, False, True, False, False, True)
+    g, G = _grids((33, 17, 49), (1 / 32,) * 3, bc)
+    k = _sphere_k(g)
+    b = _rhs(g, 11)
+    K = nn4.to_field(k, G)
+    lv = mg.Levels(g, k)
+    plan = nn4.Plan(G, K, pass_shape=shape)
+    B, X = nn4.to_field(b, G), nn4.field(G)
+    x = np.zeros(g.shape)
+    for c in range(3):
+        x = mg.vcycle(lv, x, b)
+        plan.vcycle(B, X)
+        assert _rel(nn4.nodes(X, G).cpu().numpy(), x) <= 1e-12, f"cycle {c}"
+    xref, _ = mg.pressure_solve_fcg(g, b, k=k, rtol=1e-13, max_iters=200)
+    mixed = nn4.Plan(G, K, inner=nn4.F32, outer=nn4.OUTER_FCG, inner_krylov=6, pass_shape=shape)
+    X2 = nn4.field(G)
+    info = mixed.solve(B, X2, rtol=1e-11, max_iters=60)
+    assert info["status"] == nn4.OK
+    assert _rel(nn4.nodes(X2, G).cpu().numpy(), xref) <= 1e-8
+
+
 def test_solve_fp64_fixed_cycles_history():
     """Config-1 style: 33^3 Dirichlet, 20 cycles; history and solution match the oracle."""
     need_gpu()
