@@ -124,6 +124,23 @@ def oracle_sample(n=65):
     return r
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's elapsed time (every rank gets it); the local value when world == 1."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps, world, ms_max):
+    """Solves per second of the whole job: every rank runs `steps` solves (weak scaling) and the
+    job takes the slowest rank's time."""
+    return world * steps / (ms_max / 1000.0)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -297,13 +314,9 @@ def main():
         ev1.record(stream)
         barrier()
         torch.cuda.profiler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
     ms_per = ms / args.steps
-    value = world * args.steps / (ms / 1000.0)
+    value = whole_job_rate(args.steps, world, ms)
     if args.only_mixed:
         if rank == 0:
             print(json.dumps({"n": n, "ms_per_solve": ms_per, "iterations": iters, "kernels": kernels,
