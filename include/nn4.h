@@ -130,6 +130,11 @@ typedef struct {
   int32_t coarse_entry_nodes; /* with coarse_tail: levels with at most this many nodes (0: 40000)
                             run in one cooperative launch over all SMs when the first of them has
                             more than 800 nodes */
+  int32_t fused_prolong; /* 1: in a cycle that starts from e = 0, the level-0 Jacobi sweep forms
+                            the prolonged correction itself from coarse tiles (no separate
+                            prolongation launch); 0 (default): separate launch, measured faster
+                            on GB300 (the in-tile build adds a synchronised phase to an
+                            issue-bound sweep) */
   int32_t pass_shape;    /* -1: tile shapes autotuned (autotune = 1) or the defaults.  0 ..
                             nn4_pass_shapes() - 1: that compiled tile shape for every stencil pass
                             that has it (overrides autotune; shapes compiled for FP64 only leave

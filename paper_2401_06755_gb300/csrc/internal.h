@@ -49,6 +49,11 @@ struct PassArgs {
   const float* dq;
   long long dq_pitch;  // row pitch of dq (elements)
   double* dq_out;
+  // OP_JACOBI only (optional): the input x is P ec, the trilinear prolongation of the coarse
+  // field ec (geometry gc, the grid of every second node), formed in shared memory from coarse
+  // tiles instead of read from memory (zero at Dirichlet nodes)
+  const void* ec;
+  LevelGeom gc;
 };
 
 // Stencil pass launch configuration (chosen by the autotuner or by default).
@@ -81,7 +86,7 @@ unsigned int tail_error_word();
 // ---------------------------------------------------------------- launchers
 // Tensor maps of one stencil pass: haloed tiles of x and k, pointwise tiles of b, L k, 1/diag.
 struct PassMaps {
-  CUtensorMap x, k, b, lk, invd, dq;
+  CUtensorMap x, k, b, lk, invd, dq, ec;
 };
 
 // One instance's part of a batched stencil pass (device table entry, 64-byte aligned maps).
@@ -111,6 +116,8 @@ int num_pass_cfgs();
 PassCfg pass_cfg_candidate(int index, const LevelGeom& g, int zchunk);
 int pass_box(nn4_dtype dt, const PassCfg& cfg, int* box_x, int* box_y);
 int pass_point_box(const PassCfg& cfg, int* box_x, int* box_y);
+// Box of the coarse tiles of the fused prolongation (Jacobi passes with PassArgs.ec).
+int pass_coarse_box(nn4_dtype dt, const PassCfg& cfg, int* box_x, int* box_y);
 
 // transfer.cu
 int launch_restrict(nn4_dtype dt, const void* rf, const LevelGeom& gf, void* rc,

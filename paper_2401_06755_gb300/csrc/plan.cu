@@ -513,13 +513,16 @@ PassArgs level_args(PlanImpl* P, int l, const void* b, void* out) {
 }
 
 int run_pass(PlanImpl* P, int l, int op, const void* x, const PassMaps* maps, const void* b, void* out,
-             cudaStream_t s, double* norm2 = nullptr, const float* dq = nullptr, double* dq_out = nullptr) {
+             cudaStream_t s, double* norm2 = nullptr, const float* dq = nullptr, double* dq_out = nullptr,
+             const void* ec = nullptr) {
   Level& L = P->lv[l];
   PassArgs a = level_args(P, l, b, out);
   a.norm2 = norm2;
   a.dq = dq;
   a.dq_pitch = P->g32.pitch;
   a.dq_out = dq_out;
+  a.ec = ec;
+  if (ec) a.gc = P->lv[l + 1].g;
   if (P->vc && l > 0)
     return K(P, std::string("pass27:") + opname(op) + ":" + lvl(l), s,
              [&] { return launch_pass27(P->T, op, a, x, L.a27, s); });
@@ -594,11 +597,14 @@ int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
       return rc;
     if ((rc = run_pass(P, l, OP_JACOBI, L.t, &L.m_jac, L.r, L.e, s))) return rc;
   }
-  if ((rc = K(P, "prolong:L0", s, [&] {
-         return launch_prolong_base(T, P->lv[1].e, P->lv[1].g, L0.t, first ? nullptr : F.e, L0.g, s);
-       })))
+  // a cycle from e = 0 with the plan's own maps: the level-0 sweep forms P e_1 itself
+  const bool fuse = first && F.jac_maps != nullptr && P->o.fused_prolong;
+  if (!fuse && (rc = K(P, "prolong:L0", s, [&] {
+                  return launch_prolong_base(T, P->lv[1].e, P->lv[1].g, L0.t, first ? nullptr : F.e, L0.g, s);
+                })))
     return rc;
-  return run_pass(P, 0, OP_JACOBI, L0.t, F.jac_maps, F.r, F.e, s, nullptr, F.dq, F.dq_out);
+  return run_pass(P, 0, OP_JACOBI, L0.t, F.jac_maps, F.r, F.e, s, nullptr, F.dq, F.dq_out,
+                  fuse ? P->lv[1].e : nullptr);
 }
 
 // ---------------------------------------------------------------- outer iterations
@@ -828,6 +834,10 @@ int make_level_maps(PlanImpl* P, int l) {
   const void* k = (P->vc && l == 0) ? L.k : nullptr;
   PassArgs aj = level_args(P, l, L.r, L.e);
   PassArgs ar = level_args(P, l, L.r, L.t);
+  if (l == 0 && P->lv.size() > 1 && P->o.fused_prolong) {  // coarse tiles of the fused prolongation
+    aj.ec = P->lv[1].e;
+    aj.gc = P->lv[1].g;
+  }
   if (!make_pass_maps(&L.m_jac, P->T, aj, L.cfg, L.t, k) || !make_pass_maps(&L.m_res, P->T, ar, L.cfg, L.e, k))
     return set_error(NN4_ECUDA, "tensor map encode failed");
   if (l == 0 && P->o.inner_krylov > 0)
@@ -1150,6 +1160,7 @@ void nn4_plan_opts_default(nn4_plan_opts* o) {
   o->autotune = 1;
   o->coarse_entry_nodes = 0;
   o->pass_shape = -1;
+  o->fused_prolong = 0;
 }
 
 int nn4_plan_create(const nn4_grid* g, const double* k, const nn4_plan_opts* opts, nn4_plan* out) {

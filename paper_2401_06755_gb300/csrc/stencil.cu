@@ -89,7 +89,7 @@ __device__ __forceinline__ void plane_uv(const T* __restrict__ sx, const T* __re
 // pointwise tiles (b, L k, 1/diag) of output plane p - 1, all brought by TMA onto one mbarrier,
 // so no global load sits on the critical path of a plane.
 struct Maps {
-  CUtensorMap x, k, b, lk, invd, dq;
+  CUtensorMap x, k, b, lk, invd, dq, ec;
 };
 
 template <typename T, int OP, int VC, bool ISO, int WX, int RY, int TYT, int S>
@@ -102,7 +102,11 @@ struct PassLayout {
   static constexpr int PT_PAD = (TX * TY * (int)sizeof(T) + 127) / 128 * 128;
   static constexpr int NP = (HAS_B ? 1 : 0) + (VC == 2 ? 2 : 0);
   static constexpr int DQ_PAD = OP == OP_JACOBI ? (TX * TY * 4 + 127) / 128 * 128 : 0;  // FP32 dq tile
-  static constexpr int STAGE = NF * HALO_PAD + NP * PT_PAD + DQ_PAD;
+  // OP_JACOBI: two coarse tiles (the coarse planes bracketing the fine input plane) for the fused
+  // prolongation, TX/2 + 2 AL columns from x0/2 - AL and TY/2 + 2 rows from y0/2 - 1
+  static constexpr int BXC = TX / 2 + 2 * AL, BYC = TY / 2 + 2;
+  static constexpr int CT_PAD = OP == OP_JACOBI ? (BXC * BYC * (int)sizeof(T) + 127) / 128 * 128 : 0;
+  static constexpr int STAGE = NF * HALO_PAD + NP * PT_PAD + DQ_PAD + 2 * CT_PAD;
   static constexpr size_t SMEM = (size_t)S * STAGE + S * 8 + 32 * 8;
 };
 
@@ -127,7 +131,11 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
   constexpr int NP = (HAS_B ? 1 : 0) + (VC == 2 ? 2 : 0);  // pointwise slots per stage
   constexpr int DQ_BYTES = TX * TY * 4;
   constexpr int DQ_PAD = OP == OP_JACOBI ? (DQ_BYTES + 127) / 128 * 128 : 0;
-  constexpr int STAGE = NF * HALO_PAD + NP * PT_PAD + DQ_PAD;
+  constexpr int BXC = TX / 2 + 2 * AL, BYC = TY / 2 + 2;
+  constexpr int CT_BYTES = BXC * BYC * (int)sizeof(T);
+  constexpr int CT_PAD = OP == OP_JACOBI ? (CT_BYTES + 127) / 128 * 128 : 0;
+  constexpr int CT_OFF = NF * HALO_PAD + NP * PT_PAD + DQ_PAD;  // first coarse tile in a stage
+  constexpr int STAGE = NF * HALO_PAD + NP * PT_PAD + DQ_PAD + 2 * CT_PAD;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * STAGE);
   double* red = reinterpret_cast<double*>(bars + S);
@@ -142,6 +150,7 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
   const int nplanes = ze - zs + 2;  // input planes zs-1 .. ze
   const bool use_invd = VC == 2 && OP == OP_JACOBI && a.invd != nullptr;
   const bool use_dq = OP == OP_JACOBI && a.dq != nullptr;
+  const bool use_prol = OP == OP_JACOBI && a.ec != nullptr;  // x = P ec built in shared memory
   const int pt_loads = (HAS_B ? 1 : 0) + (VC == 2 ? 1 : 0) + (use_invd ? 1 : 0);
 
   if (tid == 0) {
@@ -156,8 +165,15 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
     const int zp = mirror(zs - 1 + q, nz);
     const int kout = zs + q - 2;
     const bool pt = q >= 2;
-    mbar_expect_tx(&bars[s], NF * HALO_BYTES + (pt ? pt_loads * PT_BYTES + (use_dq ? DQ_BYTES : 0) : 0));
-    tma_load_3d(st, &maps.x, x0 - AL, y0 - 1, zp, &bars[s]);
+    mbar_expect_tx(&bars[s], (use_prol ? (NF - 1) * HALO_BYTES + 2 * CT_BYTES : NF * HALO_BYTES) +
+                                 (pt ? pt_loads * PT_BYTES + (use_dq ? DQ_BYTES : 0) : 0));
+    if (use_prol) {
+      // coarse planes zp/2 and (zp+1)/2 (the same plane for an even zp)
+      tma_load_3d(st + CT_OFF, &maps.ec, x0 / 2 - AL, y0 / 2 - 1, zp >> 1, &bars[s]);
+      tma_load_3d(st + CT_OFF + CT_PAD, &maps.ec, x0 / 2 - AL, y0 / 2 - 1, (zp + 1) >> 1, &bars[s]);
+    } else {
+      tma_load_3d(st, &maps.x, x0 - AL, y0 - 1, zp, &bars[s]);
+    }
     if (VC) tma_load_3d(st + HALO_PAD, &maps.k, x0 - AL, y0 - 1, zp, &bars[s]);
     if (pt) {
       unsigned char* pp = st + NF * HALO_PAD;
@@ -230,6 +246,39 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
     const T* tl_ = reinterpret_cast<const T*>(st + NF * HALO_PAD + (HAS_B ? PT_PAD : 0));
     const T* ti_ = tl_ + PT_PAD / sizeof(T);
     const float* tq_ = reinterpret_cast<const float*>(st + NF * HALO_PAD + NP * PT_PAD);
+    if (use_prol) {
+      // x tile = P ec on the fine columns x0-1 .. x0+TX and rows y0-1 .. y0+TY inside the grid (the
+      // only ones read: mirrored indices stay in the grid), in the prolongation kernel's order of
+      // operations (y, then x, then z) and rounded to the storage type as it stores; 0 at Dirichlet
+      // nodes.  The x region of the stage is not a copy target in this mode.
+      const int zp = mirror(zs - 1 + q, nz);
+      const bool zodd = zp & 1;
+      const bool dzf = (g.dir[4] && zp == 0) || (g.dir[5] && zp == nz - 1);
+      const T* c0 = reinterpret_cast<const T*>(st + CT_OFF);
+      const T* c1 = reinterpret_cast<const T*>(st + CT_OFF + CT_PAD);
+      T* xt = reinterpret_cast<T*>(smem + s * STAGE);
+      constexpr int FW = TX + 2, FH = TY + 2;
+      for (int e = tid; e < FW * FH; e += TX * TYT) {
+        const int fy = y0 - 1 + e / FW, fx = x0 - 1 + e % FW;
+        if (fx < 0 || fx >= nx || fy < 0 || fy >= ny) continue;
+        const int cx = (fx >> 1) - (x0 / 2 - AL), cy = (fy >> 1) - (y0 / 2 - 1);
+        const int ox = fx & 1, oy = fy & 1;
+        auto xy = [&](const T* cp) -> A {
+          const T* r0 = cp + cy * BXC + cx;
+          const T* r1 = r0 + oy * BXC;
+          const A av = A(0.5) * (to_acc(r0[0]) + to_acc(r1[0]));
+          if (!ox) return av;
+          const A an = A(0.5) * (to_acc(r0[1]) + to_acc(r1[1]));
+          return A(0.5) * (av + an);
+        };
+        A t = xy(c0);
+        if (zodd) t = A(0.5) * (t + xy(c1));
+        const bool dn = dzf || (g.dir[0] && fx == 0) || (g.dir[1] && fx == nx - 1) || (g.dir[2] && fy == 0) ||
+                        (g.dir[3] && fy == ny - 1);
+        xt[(fy - (y0 - 1)) * BX + (fx - (x0 - AL))] = from_acc<T>(dn ? A(0) : t);
+      }
+      __syncthreads();
+    }
     A ux[RY], vx[RY], xcn[RY];
     plane_uv<T, A, RY, false, ISO>(tx_, tx_, rowoff, cc, cl, cr, c, sx.p2, ux, vx, xcn);
     A ukx[RY], vkx[RY], uk[RY], vk[RY], kcn[RY];
@@ -529,6 +578,13 @@ int pass_box(nn4_dtype dt, const PassCfg& cfg, int* box_x, int* box_y) {
   return NN4_OK;
 }
 
+int pass_coarse_box(nn4_dtype dt, const PassCfg& cfg, int* box_x, int* box_y) {
+  const int al = 16 / (int)dtype_size(dt);
+  *box_x = 16 * cfg.wx + 2 * al;
+  *box_y = cfg.tyt * cfg.ry / 2 + 2;
+  return NN4_OK;
+}
+
 int pass_point_box(const PassCfg& cfg, int* box_x, int* box_y) {
   *box_x = 32 * cfg.wx;
   *box_y = cfg.tyt * cfg.ry;
@@ -546,6 +602,11 @@ bool make_pass_maps(PassMaps* m, nn4_dtype dt, const PassArgs& a, const PassCfg&
   if (a.lk) ok = ok && make_tmap_3d(&m->lk, dt, a.lk, g.nx, g.ny, g.nz, g.pitch, px, py);
   if (a.invd) ok = ok && make_tmap_3d(&m->invd, dt, a.invd, g.nx, g.ny, g.nz, g.pitch, px, py);
   if (a.dq) ok = ok && make_tmap_3d(&m->dq, NN4_F32, a.dq, g.nx, g.ny, g.nz, a.dq_pitch, px, py);
+  if (a.ec) {
+    int cx, cy;
+    pass_coarse_box(dt, cfg, &cx, &cy);
+    ok = ok && make_tmap_3d(&m->ec, dt, a.ec, a.gc.nx, a.gc.ny, a.gc.nz, a.gc.pitch, cx, cy);
+  }
   return ok;
 }
 
@@ -564,6 +625,12 @@ int launch_pass(nn4_dtype dt, int op, const PassArgs& a, const void* x, const vo
   m.lk = a.lk ? pm->lk : pm->x;
   m.invd = a.invd ? pm->invd : pm->x;
   m.dq = a.dq ? pm->dq : pm->x;
+  m.ec = a.ec ? pm->ec : pm->x;
+  if (a.ec && op != OP_JACOBI) return set_error(NN4_EINVAL, "the fused prolongation needs OP_JACOBI");
+  // (every compiled tile shape has an even height, so a tile's first row y0 sits on a coarse row)
+  if (a.ec && (a.gc.nx != (a.g.nx + 1) / 2 || a.gc.ny != (a.g.ny + 1) / 2 || a.gc.nz != (a.g.nz + 1) / 2 ||
+               !(a.g.nx & 1) || !(a.g.ny & 1) || !(a.g.nz & 1)))
+    return set_error(NN4_EINVAL, "the fused prolongation needs the grid of every second node");
   if (a.dq && (op != OP_JACOBI || !a.dq_out)) return set_error(NN4_EINVAL, "the fused dot needs OP_JACOBI and an output");
   if (op != OP_APPLY && !a.b) return set_error(NN4_EINVAL, "stencil pass needs b");
   const int vmode = vc ? (a.lk ? 2 : 1) : 0;

@@ -43,7 +43,8 @@ class _PlanOpts(ctypes.Structure):
                 ("omega", ctypes.c_double), ("use_graph", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32), ("inner_krylov", ctypes.c_int32),
                 ("coarse_tail", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("coarse_entry_nodes", ctypes.c_int32), ("pass_shape", ctypes.c_int32)]
+                ("coarse_entry_nodes", ctypes.c_int32), ("fused_prolong", ctypes.c_int32),
+                ("pass_shape", ctypes.c_int32)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -298,7 +299,7 @@ class Plan:
 
     def __init__(self, grid, k=None, inner=F64, inner_cycles=1, outer=OUTER_CYCLES, omega=2.0 / 3.0,
                  use_graph=True, check_every=1, profile=False, inner_krylov=0, coarse_tail=True, autotune=True,
-                 coarse_entry_nodes=0, pass_shape=-1):
+                 coarse_entry_nodes=0, fused_prolong=False, pass_shape=-1):
         o = _PlanOpts()
         lib().nn4_plan_opts_default(ctypes.byref(o))
         o.inner, o.inner_cycles, o.outer = int(inner), int(inner_cycles), int(outer)
@@ -309,6 +310,7 @@ class Plan:
         o.autotune = int(bool(autotune))
         o.coarse_entry_nodes = int(coarse_entry_nodes)
         o.pass_shape = int(pass_shape)
+        o.fused_prolong = int(bool(fused_prolong))
         self.grid = grid
         self.inner = inner
         self._k = k  # keep the coefficient alive while the plan exists

@@ -39,7 +39,7 @@ def test_plan_options_layout_and_shapes(nn4):
     o.coarse_entry_nodes = 123
     o.pass_shape = 7
     nn4.lib().nn4_plan_opts_default(ctypes.byref(o))
-    assert o.coarse_entry_nodes == 0 and o.pass_shape == -1 and o.autotune == 1
+    assert o.coarse_entry_nodes == 0 and o.pass_shape == -1 and o.autotune == 1 and o.fused_prolong == 0
     assert nn4.pass_shapes() == 5
 
 
