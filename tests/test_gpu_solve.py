@@ -118,7 +118,8 @@ def test_every_tile_shape(shape):
 def test_fused_prolongation_matches_separate_launch(inner):
     """The level-0 sweep that forms the prolonged correction from coarse tiles gives the solve of
     the separate prolongation launch: FP64 histories and solutions agree to 1e-12 (rounding: the
-    same operations, contracted differently), FP32/BF16 to 1e-5.  Mixed faces, ragged sizes."""
+    same operations, contracted differently), FP32/BF16 to 1e-5 (histories: plus 1e-9 absolute).
+    Mixed faces, ragged sizes."""
     need_gpu()
     nn4 = _nn4()
     g, G = _grids((65, 33, 49), (1 / 64,) * 3, (True, False, False, False, False, True))
@@ -133,8 +134,10 @@ def test_fused_prolongation_matches_separate_launch(inner):
         X = nn4.field(G)
         info = plan.solve(B, X, rtol=0.0, max_iters=5)
         out.append((np.array(info["history"]), nn4.nodes(X, G).cpu().numpy()))
-    tol = 1e-12 if inner == "f64" else 1e-5
-    assert np.all(np.abs(out[0][0] - out[1][0]) <= tol * out[1][0] + 1e-300)
+    # FP32/BF16: the inner reductions use atomics, so runs differ at the FP32 noise floor of the
+    # relative residual (~1e-11 absolute at 1e-7): a relative bound plus an absolute floor
+    tol, floor = (1e-12, 0.0) if inner == "f64" else (1e-5, 1e-9)
+    assert np.all(np.abs(out[0][0] - out[1][0]) <= tol * out[1][0] + floor)
     assert _rel(out[0][1], out[1][1]) <= tol
 
 
