@@ -75,3 +75,31 @@ def test_mass_sum_and_drift():
     m1_ref = flow.mass_sum(C.shape, h, Cn_ref)
     # the scheme is not conservative (Section 3): compare the drift, not a zero
     assert abs((m1 - m0) - (m1_ref - m0)) <= 1e-12 * abs(m0)
+
+
+def test_ten_steps_divergence_free_flow_match_oracle_and_conserve_mass():
+    """Ten volume-fraction steps in the divergence-free, wall-tangent flow of the oracle's mass pin:
+    the GPU field follows the oracle's to 1e-8 of its range and the GPU mass sum stays at its
+    initial value to 1e-9."""
+    need_gpu()
+    from paper_2401_06755_gb300 import nn4
+    from synth import sphere_ramp_field
+    n, h = (33, 9, 33), (1 / 32,) * 3
+    x, y, z = node_coords(n, h)
+    A = 0.25
+    u = A * np.sin(np.pi * x) ** 2 * 2 * np.pi * np.sin(np.pi * z) * np.cos(np.pi * z)
+    w = -A * 2 * np.pi * np.sin(np.pi * x) * np.cos(np.pi * x) * np.sin(np.pi * z) ** 2
+    v = np.zeros_like(u)
+    C = sphere_ramp_field(n, h, (0.5, 0.125, 0.35), 0.2, 2 * h[0])
+    dt = 0.2 * h[0] / max(np.abs(u).max(), np.abs(w).max())
+    G = nn4.Grid(n, h)
+    Cd = nn4.to_field(C, G)
+    U, V, W = (nn4.to_field(a, G) for a in (u, v, w))
+    m0 = float(nn4.mass_sum(G, Cd).item())
+    for _ in range(10):
+        _, C, _ = flow.vof_step(C.shape, h, C, u, v, w, dt)
+        _, Cd = nn4.vof_advect_residual(G, Cd, U, V, W, dt)
+    Cg = nn4.nodes(Cd, G).cpu().numpy()
+    assert np.abs(Cg - C).max() <= 1e-8 * (C.max() - C.min())
+    assert abs(float(nn4.mass_sum(G, Cd).item()) - m0) <= 1e-9 * m0
+
