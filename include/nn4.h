@@ -87,6 +87,17 @@ int nn4_residual(const nn4_grid* g, nn4_dtype dt, const void* b, const void* x, 
 int nn4_restrict(const nn4_grid* fine, nn4_dtype dt, const void* r_fine, void* r_coarse,
                  void* stream);
 
+/* r_coarse = R (b - A x): the residual of nn4_residual restricted as by nn4_restrict, in one
+ * pass that does not store the fine residual (the start of every V-cycle whose correction is not
+ * zero; Section 2.4 and Eq. ph_disc).  If norm2 != NULL it is a device double overwritten with
+ * sum over fine nodes of (b - A x)^2 (FP64 across blocks).  Grids, pitches and k as for
+ * nn4_residual and nn4_restrict; every n must be odd and >= 3.  The fine residual is computed in
+ * FP32 for F32 / BF16 storage and rounded to the storage type once, on the coarse value, so its
+ * result can differ from nn4_residual followed by nn4_restrict by that rounding.  r_coarse must
+ * not alias b, x or k. */
+int nn4_residual_restrict(const nn4_grid* fine, nn4_dtype dt, const void* b, const void* x,
+                          const void* k, void* r_coarse, double* norm2, void* stream);
+
 /* e_fine = P e_coarse (accumulate = 0) or e_fine += P e_coarse (accumulate != 0), P the
  * trilinear interpolation (injection at even nodes, averages of 2, 4 or 8 coarse nodes
  * elsewhere); fine Dirichlet nodes are set to 0 (accumulate = 0) or left unchanged.  Coarse

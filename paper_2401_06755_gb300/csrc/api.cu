@@ -171,7 +171,7 @@ const char* nn4_version(void) { return "nn4-gb300 0.1 (sm_103a)"; }
 int nn4_device_error(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return check_cuda(e, "device synchronise");
-  const unsigned int w = stencil_error_word() | flow_error_word() | tail_error_word();
+  const unsigned int w = stencil_error_word() | flow_error_word() | tail_error_word() | restrict_error_word();
   if (w & 1u) return set_error(NN4_ETIMEOUT, "a bounded device wait gave up");
   if (w & 2u) return set_error(NN4_EBOUNDS, "a checked device index was out of range");
   return NN4_OK;
@@ -245,6 +245,31 @@ int nn4_restrict(const nn4_grid* fine, nn4_dtype dt, const void* r_fine, void* r
   LevelGeom gf = geom_of(fine);
   LevelGeom gc = coarse_geom(gf, dt);
   return launch_restrict(dt, r_fine, gf, r_coarse, gc, static_cast<cudaStream_t>(stream));
+}
+
+int nn4_residual_restrict(const nn4_grid* fine, nn4_dtype dt, const void* b, const void* x, const void* k,
+                          void* r_coarse, double* norm2, void* stream) {
+  int rc;
+  if ((rc = validate_grid(fine, dt, 3)) || (rc = validate_ptr(b, "b")) || (rc = validate_ptr(x, "x")) ||
+      (rc = validate_ptr(r_coarse, "r_coarse")))
+    return rc;
+  if (k && (rc = validate_ptr(k, "k"))) return rc;
+  for (int d = 0; d < 3; ++d)
+    if (fine->n[d] % 2 == 0) return set_error(NN4_EINVAL, "restriction needs an odd node count on every axis");
+  if (r_coarse == x || r_coarse == b || r_coarse == k) return set_error(NN4_EINVAL, "r_coarse must not alias b, x or k");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (norm2) {
+    if ((rc = check_cuda(cudaMemsetAsync(norm2, 0, sizeof(double), s), "zero norm"))) return rc;
+  }
+  PassArgs a{};
+  a.g = geom_of(fine);
+  a.L = stencil_coef(fine->h);
+  a.b = b;
+  a.out = r_coarse;
+  a.norm2 = norm2;
+  a.gc = coarse_geom(a.g, dt);
+  a.zchunk = rr_default_zchunk(a.gc, 1216);
+  return launch_residual_restrict(dt, a, x, k, s);
 }
 
 int nn4_prolong(const nn4_grid* fine, nn4_dtype dt, const void* e_coarse, void* e_fine, int accumulate,

@@ -143,14 +143,13 @@ struct BatchImpl {
     int count = 0, total = 0;
   };
   std::vector<PassSet> jac;       // Jacobi at slot l (l < tail_start of the instance)
-  PassSet res0;                   // level-0 residual (inner, cycles >= 2)
+  PassSet rr0;                    // level-0 residual + restriction (inner, cycles >= 2)
   PassSet res64;                  // FP64 outer residual
   struct XferSet {
     BatchXfer* d = nullptr;
     int count = 0, total = 0;
   };
   std::vector<XferSet> restr;     // restriction slot l -> l+1
-  XferSet restr0_from_t;          // level 0 -> 1 from the fine residual t (cycles >= 2)
   std::vector<XferSet> prol;      // prolongation slot l+1 -> l
   XferSet prol0_base;             // finest prolongation with base e (cycles >= 2)
   TailArgs* tails = nullptr;
@@ -300,6 +299,29 @@ int make_pass(BatchImpl* B, std::vector<BatchPass>& v, nn4_dtype dt, int inst, c
   return NN4_OK;
 }
 
+// Level-0 residual + restriction of one instance: out (level 1's r) = R (b - A x).
+int make_rr_pass(std::vector<BatchPass>& v, nn4_dtype dt, int inst, const LevelGeom& g, const Coef8& L,
+                 const LevelGeom& gc, const void* x, const void* b, void* out, int* total) {
+  if (!(g.nx & 1) || !(g.ny & 1) || !(g.nz & 1) || gc.nx != (g.nx + 1) / 2 || gc.ny != (g.ny + 1) / 2 ||
+      gc.nz != (g.nz + 1) / 2)
+    return set_error(NN4_EINVAL, "residual + restriction needs odd node counts and the grid of every second node");
+  BatchPass bp;
+  std::memset(&bp, 0, sizeof(bp));
+  bp.args.g = g;
+  bp.args.L = L;
+  bp.args.b = b;
+  bp.args.out = out;
+  bp.args.gc = gc;
+  // as for the other batched passes: enough short items per instance, at most 16 coarse planes
+  bp.args.zchunk = std::min(rr_default_zchunk(gc, 64), 16);
+  if (!make_rr_maps(&bp.maps, dt, bp.args, x, nullptr)) return set_error(NN4_ECUDA, "tensor map encode failed");
+  bp.inst = inst;
+  bp.first = *total;
+  *total += rr_batch_tiles(&bp);
+  v.push_back(bp);
+  return NN4_OK;
+}
+
 void make_xfer(std::vector<BatchXfer>& v, int inst, bool prolong, const LevelGeom& gf, const LevelGeom& gc,
                const void* src, void* dst, const void* base, int* total) {
   BatchXfer X;
@@ -319,12 +341,9 @@ void make_xfer(std::vector<BatchXfer>& v, int inst, bool prolong, const LevelGeo
 int bcycle(BatchImpl* B, bool first, cudaStream_t s, int64_t* kernels) {
   const nn4_dtype T = B->T;
   int rc;
-  if (!first) {
-    if ((rc = launch_pass_batch(T, OP_RESIDUAL, B->res0.d, B->res0.count, B->res0.total, B->active, s))) return rc;
-    if ((rc = launch_xfer_batch(T, false, B->restr0_from_t.d, B->restr0_from_t.count, B->restr0_from_t.total,
-                                B->active, s)))
-      return rc;
-    *kernels += 2;
+  if (!first) {  // level 1's right-hand side R (r - A e) in one pass
+    if ((rc = launch_rr_batch(T, B->rr0.d, B->rr0.count, B->rr0.total, B->active, s))) return rc;
+    *kernels += 1;
   } else {
     if ((rc = launch_xfer_batch(T, false, B->restr[0].d, B->restr[0].count, B->restr[0].total, B->active, s)))
       return rc;
@@ -479,15 +498,15 @@ int nn4_batch_create(const nn4_grid* grids, int32_t count, const nn4_plan_opts* 
   // tables of every batched launch
   const nn4_dtype T = B->T;
   std::vector<std::vector<BatchPass>> jac(B->maxlev);
-  std::vector<BatchPass> res0, res64;
+  std::vector<BatchPass> rr0, res64;
   std::vector<std::vector<BatchXfer>> restr(B->maxlev), prol(B->maxlev);
-  std::vector<BatchXfer> restr0t, prol0b;
+  std::vector<BatchXfer> prol0b;
   std::vector<TailArgs> tails(count);
   std::vector<BOuter> outer(count);
   B->jac.resize(B->maxlev);
   B->restr.resize(B->maxlev);
   B->prol.resize(B->maxlev);
-  int tot_res0 = 0, tot_res64 = 0, tot_r0t = 0, tot_p0b = 0;
+  int tot_rr0 = 0, tot_res64 = 0, tot_p0b = 0;
   std::vector<int> tot_jac(B->maxlev, 0), tot_restr(B->maxlev, 0), tot_prol(B->maxlev, 0);
   int rowblocks = 0;
   for (int i = 0; i < count; ++i) {
@@ -500,8 +519,7 @@ int nn4_batch_create(const nn4_grid* grids, int32_t count, const nn4_plan_opts* 
       make_xfer(prol[l], i, true, L.g, I.lv[l + 1].g, I.lv[l + 1].e, L.t, nullptr, &tot_prol[l]);
     }
     BLevel& L0 = I.lv[0];
-    if ((rc = make_pass(B, res0, T, i, L0.g, L0.L, L0.e, L0.r, L0.t, o.omega, nullptr, &tot_res0))) return fail(rc);
-    make_xfer(restr0t, i, false, L0.g, I.lv[1].g, L0.t, I.lv[1].r, nullptr, &tot_r0t);
+    if ((rc = make_rr_pass(rr0, T, i, L0.g, L0.L, I.lv[1].g, L0.e, L0.r, I.lv[1].r, &tot_rr0))) return fail(rc);
     make_xfer(prol0b, i, true, L0.g, I.lv[1].g, I.lv[1].e, L0.t, L0.e, &tot_p0b);
     if ((rc = make_pass(B, res64, NN4_F64, i, I.g64, I.L64, I.x64, I.b64, I.r64, o.omega, B->rn + i, &tot_res64)))
       return fail(rc);
@@ -543,16 +561,14 @@ int nn4_batch_create(const nn4_grid* grids, int32_t count, const nn4_plan_opts* 
     B->prol[l].count = (int)prol[l].size();
     B->prol[l].total = tot_prol[l];
   }
-  if ((rc = upload(B, res0, &B->res0.d)) || (rc = upload(B, res64, &B->res64.d)) ||
-      (rc = upload(B, restr0t, &B->restr0_from_t.d)) || (rc = upload(B, prol0b, &B->prol0_base.d)) ||
+  if ((rc = upload(B, rr0, &B->rr0.d)) || (rc = upload(B, res64, &B->res64.d)) ||
+      (rc = upload(B, prol0b, &B->prol0_base.d)) ||
       (rc = upload(B, tails, &B->tails)) || (rc = upload(B, outer, &B->outer)))
     return fail(rc);
-  B->res0.count = count;
-  B->res0.total = tot_res0;
+  B->rr0.count = count;
+  B->rr0.total = tot_rr0;
   B->res64.count = count;
   B->res64.total = tot_res64;
-  B->restr0_from_t.count = count;
-  B->restr0_from_t.total = tot_r0t;
   B->prol0_base.count = count;
   B->prol0_base.total = tot_p0b;
   B->outer_blocks = rowblocks;

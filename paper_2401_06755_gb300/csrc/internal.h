@@ -28,7 +28,9 @@ struct LevelGeom {
 // OP_APPLY: out = A x.  OP_RESIDUAL: out = b - A x (0 at Dirichlet nodes), norm2 += out^2.
 // OP_JACOBI: out = x + omega D^-1 (b - A x) (x at Dirichlet nodes).
 // OP_MATVEC: out = A x (0 at Dirichlet nodes), norm2 += x.out, dot2 += x.b.
-enum PassOp { OP_APPLY = 0, OP_RESIDUAL = 1, OP_JACOBI = 2, OP_MATVEC = 3 };
+// OP_RESIDUAL_RESTRICT: out = R (b - A x) on the coarse grid gc (0 at coarse Dirichlet nodes),
+// norm2 += sum over fine nodes of (b - A x)^2; zchunk counts coarse planes per block.
+enum PassOp { OP_APPLY = 0, OP_RESIDUAL = 1, OP_JACOBI = 2, OP_MATVEC = 3, OP_RESIDUAL_RESTRICT = 4 };
 
 struct PassArgs {
   LevelGeom g;
@@ -53,7 +55,7 @@ struct PassArgs {
   // field ec (geometry gc, the grid of every second node), formed in shared memory from coarse
   // tiles instead of read from memory (zero at Dirichlet nodes)
   const void* ec;
-  LevelGeom gc;
+  LevelGeom gc;  // the coarse grid (fused prolongation; residual + restriction)
 };
 
 // Stencil pass launch configuration (chosen by the autotuner or by default).
@@ -82,6 +84,7 @@ long long resident_grid(const void* kern, int threads, size_t smem, long long wa
 unsigned int stencil_error_word();
 unsigned int flow_error_word();
 unsigned int tail_error_word();
+unsigned int restrict_error_word();
 
 // ---------------------------------------------------------------- launchers
 // Tensor maps of one stencil pass: haloed tiles of x and k, pointwise tiles of b, L k, 1/diag.
@@ -110,7 +113,20 @@ PassCfg batch_pass_cfg(nn4_dtype dt);
 // TMA; the maps are built here unless `maps` is given (built with make_pass_maps for this cfg).
 int launch_pass(nn4_dtype dt, int op, const PassArgs& a, const void* x, const void* k,
                 const PassCfg& cfg, cudaStream_t s, const PassMaps* maps = nullptr);
-bool make_pass_maps(PassMaps* m, nn4_dtype dt, const PassArgs& a, const PassCfg& cfg, const void* x, const void* k);
+// wide_point: the pointwise boxes are 32 wx + 16/sizeof(T) wide (OP_RESIDUAL_RESTRICT's shifted tiles)
+bool make_pass_maps(PassMaps* m, nn4_dtype dt, const PassArgs& a, const PassCfg& cfg, const void* x, const void* k,
+                    bool wide_point = false);
+
+// resrestrict.cu: out = R (b - A x) on the coarse grid a.gc and norm2 += ||b - A x||^2 in one pass
+// (a.zchunk = coarse planes per CTA, see rr_default_zchunk); maps from make_rr_maps, or built here.
+int launch_residual_restrict(nn4_dtype dt, const PassArgs& a, const void* x, const void* k, cudaStream_t s,
+                             const PassMaps* maps = nullptr);
+bool make_rr_maps(PassMaps* m, nn4_dtype dt, const PassArgs& a, const void* x, const void* k);
+PassCfg rr_pass_cfg();
+int rr_default_zchunk(const LevelGeom& gc, int min_ctas);
+// Fills the tiling fields of a batch entry (args.gc and args.zchunk set) and returns its item count.
+int rr_batch_tiles(BatchPass* bp);
+int launch_rr_batch(nn4_dtype dt, const BatchPass* items, int count, int total, const int* active, cudaStream_t s);
 PassCfg default_pass_cfg(nn4_dtype dt, bool vc, const LevelGeom& g);
 int num_pass_cfgs();
 PassCfg pass_cfg_candidate(int index, const LevelGeom& g, int zchunk);

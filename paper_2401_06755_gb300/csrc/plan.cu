@@ -35,6 +35,7 @@ struct Level {
   void* e = nullptr;  // correction (output of the Jacobi sweep)
   void* t = nullptr;  // prolongated correction / fine residual (input of the Jacobi sweep)
   PassMaps m_jac{}, m_res{};  // Jacobi (x = t, b = r) and residual (x = e, b = r) passes
+  PassMaps m_rr{};            // level 0: residual + restriction (x = e, b = r, out = level 1's r)
   PassMaps m_jac_dq[2]{};     // level 0 with the inner Krylov loop: Jacobi + the fused dot with q[parity]
   void* a27 = nullptr;  // Galerkin coefficients (coefficient field, levels >= 1)
   void* k = nullptr;    // coefficient field in the inner type (level 0)
@@ -490,6 +491,7 @@ struct Fine {
   void* e;
   const PassMaps* res_maps;  // residual pass on (e, r); NULL: built per launch
   const PassMaps* jac_maps;  // level-0 Jacobi pass (t, r); NULL: built per launch
+  const PassMaps* rr_maps = nullptr;  // residual + restriction on (e, r); NULL: built per launch
   const float* dq = nullptr;  // optional: the final level-0 sweep also adds e.dq to *dq_out
   double* dq_out = nullptr;
 };
@@ -531,6 +533,15 @@ int run_pass(PlanImpl* P, int l, int op, const void* x, const PassMaps* maps, co
            [&] { return launch_pass(P->T, op, a, x, vc0 ? L.k : nullptr, L.cfg, s, maps); });
 }
 
+// Arguments of the level-0 residual + restriction pass (b = r, output level 1's right-hand side).
+PassArgs rr_args(PlanImpl* P, const void* r) {
+  PassArgs a = level_args(P, 0, r, P->lv[1].r);
+  a.invd = nullptr;
+  a.gc = P->lv[1].g;
+  a.zchunk = rr_default_zchunk(a.gc, 1216);
+  return a;
+}
+
 int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
   const int nl = (int)P->lv.size();
   const nn4_dtype T = P->T;
@@ -542,14 +553,17 @@ int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
     if ((rc = run_pass(P, 0, OP_RESIDUAL, F.e, F.res_maps, F.r, L0.t, s))) return rc;
     return K(P, "coarsest", s, [&] { return launch_coarse_solve(T, P->ainv, P->free_idx, P->nfree, L0.t, F.e, L0.g, 1, s); });
   }
-  // down: fine residual, then restriction to the coarsest level
-  const void* r0 = F.r;
-  if (!first) {
-    if ((rc = run_pass(P, 0, OP_RESIDUAL, F.e, F.res_maps, F.r, L0.t, s))) return rc;
-    r0 = L0.t;
+  // down: level 1's right-hand side R (r - A e), then restriction to the coarsest level
+  if (first) {  // e = 0: the fine residual is r itself
+    if ((rc = K(P, "restrict:L0", s, [&] { return launch_restrict(T, F.r, L0.g, P->lv[1].r, P->lv[1].g, s); })))
+      return rc;
+  } else {  // one pass; the fine residual is not stored
+    PassArgs a = rr_args(P, F.r);
+    if ((rc = K(P, "residual_restrict:L0", s, [&] {
+           return launch_residual_restrict(T, a, F.e, P->vc ? L0.k : nullptr, s, F.rr_maps);
+         })))
+      return rc;
   }
-  if ((rc = K(P, "restrict:L0", s, [&] { return launch_restrict(T, r0, L0.g, P->lv[1].r, P->lv[1].g, s); })))
-    return rc;
   const int ts = P->tail_start > 0 ? P->tail_start : nl;  // levels >= ts run in one launch
   const int top = P->coarse_coop ? P->coarse_top : -1;     // its transfers run there too
   const int host_down = top > 0 ? top : ts;                // host restrictions end at this level
@@ -613,6 +627,7 @@ int vcycle_impl(PlanImpl* P, const Fine& F, bool first, cudaStream_t s) {
 int inner_solve(PlanImpl* P, cudaStream_t s, int dq_par = -1) {
   Level& L0 = P->lv[0];
   Fine F{L0.r, L0.e, &L0.m_res, &L0.m_jac};
+  F.rr_maps = &L0.m_rr;
   int rc;
   for (int c = 0; c < P->o.inner_cycles; ++c) {
     Fine Fc = F;
@@ -839,6 +854,8 @@ int make_level_maps(PlanImpl* P, int l) {
     aj.gc = P->lv[1].g;
   }
   if (!make_pass_maps(&L.m_jac, P->T, aj, L.cfg, L.t, k) || !make_pass_maps(&L.m_res, P->T, ar, L.cfg, L.e, k))
+    return set_error(NN4_ECUDA, "tensor map encode failed");
+  if (l == 0 && P->lv.size() > 1 && !make_rr_maps(&L.m_rr, P->T, rr_args(P, L.r), L.e, k))
     return set_error(NN4_ECUDA, "tensor map encode failed");
   if (l == 0 && P->o.inner_krylov > 0)
     for (int t = 0; t < 2; ++t) {

@@ -99,6 +99,7 @@ def lib():
             "nn4_stencil_apply": (ctypes.c_int, [G, ctypes.c_int, vp, vp, vp, vp]),
             "nn4_residual": (ctypes.c_int, [G, ctypes.c_int, vp, vp, vp, vp, vp, vp]),
             "nn4_restrict": (ctypes.c_int, [G, ctypes.c_int, vp, vp, vp]),
+            "nn4_residual_restrict": (ctypes.c_int, [G, ctypes.c_int, vp, vp, vp, vp, vp, vp]),
             "nn4_prolong": (ctypes.c_int, [G, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
             "nn4_jacobi_smooth": (ctypes.c_int, [G, ctypes.c_int, vp, vp, vp, vp, dbl, vp]),
             "nn4_plan_opts_default": (None, [ctypes.POINTER(_PlanOpts)]),
@@ -229,6 +230,15 @@ def restrict(grid, r_fine, r_coarse=None, stream=None):
         r_coarse = field(grid.coarse(), r_fine.dtype, r_fine.device)
     g = grid.c(r_fine.dtype)
     _check(lib().nn4_restrict(ctypes.byref(g), _dt(r_fine), _ptr(r_fine), _ptr(r_coarse), _stream(stream)))
+    return r_coarse
+
+
+def residual_restrict(grid, b, x, k=None, r_coarse=None, norm2=None, stream=None):
+    if r_coarse is None:
+        r_coarse = field(grid.coarse(), x.dtype, x.device)
+    g = grid.c(x.dtype)
+    _check(lib().nn4_residual_restrict(ctypes.byref(g), _dt(x), _ptr(b), _ptr(x), _ptr(k), _ptr(r_coarse),
+                                       _ptr(norm2), _stream(stream)))
     return r_coarse
 
 

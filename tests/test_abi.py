@@ -67,6 +67,9 @@ def test_host_validation_rejects_bad_arguments(nn4):
     assert L.nn4_residual(ctypes.byref(bad), nn4.F64, p, p, null, p, null, null) == nn4.EINVAL
     even = nn4.Grid((8, 9, 9), (0.125,) * 3).c(nn4.F64)
     assert L.nn4_restrict(ctypes.byref(even), nn4.F64, p, ctypes.c_void_p(8192), null) == nn4.EINVAL
+    assert L.nn4_residual_restrict(ctypes.byref(even), nn4.F64, p, p, null, ctypes.c_void_p(8192), null,
+                                   null) == nn4.EINVAL
+    assert L.nn4_residual_restrict(ctypes.byref(g), nn4.F64, p, p, null, p, null, null) == nn4.EINVAL  # alias
     # misaligned pointer
     assert L.nn4_stencil_apply(ctypes.byref(g), nn4.F64, ctypes.c_void_p(4100), null,
                                ctypes.c_void_p(8192), null) == nn4.EINVAL

@@ -93,6 +93,71 @@ def test_restrict_prolong(gi, dt):
     _cmp(ef2, ref2, np.abs(x) + mg.prolong_raw(gc, np.abs(ec)), dt)
 
 
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("vc", [False, True])
+@pytest.mark.parametrize("gi", [0, 1, 2, 3, 4])
+def test_residual_restrict_fused(gi, vc, dt):
+    """R (b - A x) in one pass against the oracle's restriction of its residual, element by element
+    on the coarse grid (several tiles and z-chunks, ragged in every axis, every face mix), and the
+    fine residual's squared norm against the oracle's."""
+    need_gpu()
+    n, h, bc = GRIDS[gi]
+    nn4, g, G, x, b, k, X, B, K = _setup(n, h, bc, dt, vc, seed=20 + gi)
+    norm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rc = nn4.nodes(nn4.residual_restrict(G, B, X, K, norm2=norm), G.coarse()).double().cpu().numpy()
+    rf = mg.residual(g, b, x, k)
+    ebound = abs_bound(g, x, k) + np.abs(b)  # per fine node: the residual's rounding scale
+    _cmp(rc, mg.restrict(g, rf), mg.restrict_raw(g, ebound), dt)
+    # the fine residual is not rounded to the storage type here: FP32 (FP64) arithmetic only, then
+    # FP32 partial sums along each thread's z-march
+    tol = TOL["f32"] if dt != "f64" else TOL["f64"]
+    nref = float((rf * rf).sum())
+    lim = 2 * tol * float((np.abs(rf) * ebound).sum()) + 3 * tol * nref + 1e-300
+    assert abs(norm.item() - nref) <= lim, (norm.item(), nref)
+
+
+def test_full_size_residual_restrict_sampled():
+    """257^3 FP32 residual + restriction with a coefficient field, checked at sampled coarse nodes
+    against the oracle's residual on a 7^3 window around each sample, restricted by hand."""
+    need_gpu()
+    from paper_2401_06755_gb300 import nn4
+    n = 257
+    h = 1.0 / 256
+    G = nn4.Grid((n,) * 3, (h,) * 3)
+    rng = np.random.default_rng(6)
+    shape = (n, n, n)
+    x = rounded(rng.standard_normal(shape), "f32")
+    k = rounded(np.exp(rng.standard_normal(shape)), "f32")
+    b = rounded(rng.standard_normal(shape) * h ** 3, "f32")
+    dev = lambda a: nn4.to_field(a, G, torch.float32)
+    rc = nn4.nodes(nn4.residual_restrict(G, dev(b), dev(x), dev(k)), G.coarse()).double().cpu().numpy()
+    nc = (n + 1) // 2
+    pts = [(0, 0, 0), (128, 128, 128), (64, 0, 127), (15, 7, 17), (14, 6, 16), (0, 100, 8)] + \
+        [tuple(int(v) for v in rng.integers(0, nc, 3)) for _ in range(30)]
+    w1 = {-1: 0.5, 0: 1.0, 1: 0.5}
+    for (I, J, Kc) in pts:
+        c = (2 * Kc, 2 * J, 2 * I)
+        # fine residuals at c + {-1, 0, 1}^3 are exact on a window reaching two nodes past them
+        lo = [max(0, v - 3) for v in c]
+        hi = [min(n, v + 4) for v in c]
+        sl = tuple(slice(a, b_) for a, b_ in zip(lo, hi))
+        sub = mg.Grid(tuple(hi[2 - d] - lo[2 - d] for d in range(3)), (h,) * 3)
+        rs = mg.residual(sub, b[sl], x[sl], k[sl])
+        es = abs_bound(sub, x[sl], k[sl]) + np.abs(b[sl])
+        val = bnd = 0.0
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    f = (c[0] + dz, c[1] + dy, c[2] + dx)
+                    if not all(0 <= f[d] < n for d in range(3)):
+                        continue
+                    wgt = w1[dz] * w1[dy] * w1[dx]
+                    li = tuple(f[d] - lo[d] for d in range(3))
+                    val += wgt * rs[li]
+                    bnd += wgt * es[li]
+        assert abs(rc[Kc, J, I] - val) <= TOL["f32"] * (bnd + abs(val)), (I, J, Kc)
+
+
 def test_full_size_stencil_sampled():
     """257^3 FP32 stencil apply with a coefficient field (the timed size), checked at sampled
     nodes against the oracle evaluated on a small neighbourhood of each sample."""
