@@ -106,8 +106,8 @@ int nn4_prolong(const nn4_grid* fine, nn4_dtype dt, const void* e_coarse, void* 
                 int accumulate, void* stream);
 
 /* One weighted-Jacobi sweep x_out = x_in + omega D^-1 (b - A x_in) at free nodes; Dirichlet
- * nodes are copied.  D is the exact diagonal of A (boundary rows included).  Section 1.1
- * ("multigrid with Jacobi smoothing").  x_out must not alias x_in. */
+ * nodes are copied.  D is the exact diagonal of A (boundary rows included).  Section 1.1 (the
+ * multigrid solver smooths with Jacobi iterations).  x_out must not alias x_in. */
 int nn4_jacobi_smooth(const nn4_grid* g, nn4_dtype dt, const void* b, const void* k,
                       const void* x_in, void* x_out, double omega, void* stream);
 

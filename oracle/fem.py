@@ -1,11 +1,11 @@
 """Q1 finite-element integrals and matrix-free assembled operators (ORACLE, test use only).
 
 Section 2.2.3 defines filter weights as integrals of products of basis functions and their
-derivatives "in the usual manner"; Section 2.2.4 uses the same construction for the second
+derivatives, built the standard finite-element way; Section 2.2.4 uses the same construction for the second
 derivative (Laplacian) filter.  Here the integrals are taken element by element with 2-point
 Gauss quadrature per axis (exact for the bilinear-per-axis integrands of Q1), and a global
 operator is applied by summing element contributions, which is what assembly means.  Near the
-domain boundary a node simply has fewer elements around it (natural, "do nothing" boundary).
+domain boundary a node simply has fewer elements around it (a natural boundary: no boundary term is added).
 
 Arrays are indexed [z, y, x] (x fastest).  Local element node a = ax + 2*ay + 4*az.
 """

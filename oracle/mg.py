@@ -16,7 +16,7 @@ prolongation, sweep counts or the coarsest solve, so this module takes the follo
 * one sawtooth V(0,1) cycle: residual on the finest level, restriction to the coarsest level,
   exact coarsest solve, then on the way up prolongation followed by one weighted-Jacobi sweep
   (omega = 2/3) on every level, the finest level included;
-* Dirichlet nodes (the paper's halo "set to the desired value", Section 2.3.3) are stored in the
+* Dirichlet nodes (the paper fixes the halo to the prescribed value there, Section 2.3.3) are stored in the
   array and never change; their residual and correction are zero.  Zero-derivative faces use
   natural FE truncation (the boundary row of the assembled operator).
 
