@@ -613,6 +613,7 @@ def bytes_per_node(name, s):
         "restrict:L0": 1.125 * s,      # per fine node: fine read, 1/8 coarse written
         "prolong:L0": 1.125 * s,       # per fine node: fine written, 1/8 coarse read
         "pass27:jacobi:L1": 30.0 * s,  # per level-1 node: 27 coefficients, x (haloed), b read, e written
+        "residual_restrict:L0": 4.125 * s,  # per fine node: x (haloed), k, b, L k read; 1/8 coarse written
     }
     return table.get(name)
 
@@ -622,7 +623,8 @@ _PASS = ("stencil.cu", "pass_tile.cuh")
 KERNEL_SOURCE = {"pass64:matvec": _PASS, "pass64:residual": _PASS, "pass:jacobi:L0": _PASS,
                  "inner:matvec": _PASS, "inner:update": ("outer.cu",), "inner:direction": ("outer.cu",),
                  "inner:dot": ("outer.cu",), "restrict:L0": ("transfer.cu",), "prolong:L0": ("transfer.cu",),
-                 "pass27:jacobi:L1": ("galerkin.cu",), "coarse_levels": ("tail.cu",)}
+                 "pass27:jacobi:L1": ("galerkin.cu",), "coarse_levels": ("tail.cu",),
+                 "residual_restrict:L0": ("resrestrict.cu", "pass_tile.cuh")}
 
 
 def _source_sha(files):
