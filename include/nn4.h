@@ -192,8 +192,8 @@ typedef struct {
 /* Solves A x = b (FP64 device arrays on the plan's grid, pitch g->pitch) from the x given,
  * until ||b - A x||_2 / ||b||_2 <= rtol or max_iters outer iterations.  Synchronises the stream.
  * Returns NN4_ENOCONV (with info filled) when the cap is reached, NN4_ENONFINITE for a
- * non-finite norm.  Section 2.4 Stage 1 and Stage 3 ("forced to zero using the U-Net multigrid
- * solver"). */
+ * non-finite norm.  Section 2.4, Stages 1 and 3 (the pressure residual driven to zero by the
+ * U-Net multigrid). */
 int nn4_pressure_solve(nn4_plan p, const double* b, double* x, double rtol, int32_t max_iters,
                        nn4_solve_info* info, void* stream);
 
