@@ -253,6 +253,10 @@ def main():
     ap.add_argument("--residual-restrict", action="store_true",
                     help="time the fused residual + restriction against residual then restriction at n^3 "
                          "(one JSON line; no solve)")
+    ap.add_argument("--flow-kernels", action="store_true",
+                    help="time each explicit multiphase entry point on the 513^3 rising-bubble grid "
+                         "(one JSON line; no solve)")
+    ap.add_argument("--flow-n", type=int, default=513, help="nodes per axis for --flow-kernels")
     ap.add_argument("--ncu-summary", metavar="CSV", help="summarise an ncu launch list of the timed region")
     ap.add_argument("--write-traffic", action="store_true", help="with --ncu-summary: write profiles/ncu_traffic.json")
     args = ap.parse_args()
@@ -268,6 +272,9 @@ def main():
         return
     if args.residual_restrict:
         run_residual_restrict(args)
+        return
+    if args.flow_kernels:
+        run_flow_kernels(args)
         return
 
     import torch
@@ -503,6 +510,85 @@ def run_residual_restrict(args):
         P.close()
     print(json.dumps({"metric": "residual_restrict_us", "unit": "us", "n": n, "steps": args.steps,
                       "warmup": args.warmup, "l2_flush": True, "results": res}), flush=True)
+
+
+# ---------------------------------------------------------------- explicit multiphase terms
+# compulsory bytes per node of each entry point: every input field read once, every output written once
+FLOW_BYTES = {"vof_advect_residual": 48,   # C, u, v, w read; s_C, C_next written
+              "momentum_sources": 40,      # C read; s_x, s_y, s_z, kappa written
+              "momentum_predict": 136,     # C, u^n, u^{n+1/2}, p, s read; u~ written; u^{n+1/2} rewritten
+              "pressure_rhs_hs": 32,       # s read; b written
+              "pressure_rhs_nh": 48,       # C, u~ read; b, rho written
+              "velocity_correct": 80,      # C, dp read; u read and written; p_nh read and written
+              "mass_sum": 8}               # C read
+
+
+def run_flow_kernels(args):
+    """Device time of each explicit multiphase entry point (FP64) on the rising-bubble grid of
+    n^3 nodes on the unit cube (bubble radius 0.25 at (0.5, 0.5, 0.3), ramp 2h, densities
+    1000/1, viscosities 10/0.1, sigma 1.96, g 0.98, dt 1e-4), velocities a smooth field that
+    vanishes on the no-slip walls.  Each figure is the median of `steps` launches after `warmup`;
+    the fields (1 GB each at 513^3) are far larger than L2.  Bandwidth is counted from the
+    compulsory bytes of FLOW_BYTES against the measured copy bandwidth; the volume-fraction and
+    momentum steps are FP64-arithmetic-bound, so their fraction is low by design."""
+    import math
+    import torch
+    from paper_2401_06755_gb300 import nn4
+    n = args.flow_n
+    h = 1.0 / (n - 1)
+    Gv = nn4.Grid((n, n, n), (h, h, h), (nn4.DIRICHLET,) * 6)
+    Gc = nn4.Grid((n, n, n), (h, h, h))
+    Gp = nn4.Grid((n, n, n), (h, h, h), (nn4.NATURAL,) * 5 + (nn4.DIRICHLET,))
+    fp = nn4.flow_params(1e-4, rho_l=1000.0, rho_g=1.0, mu_l=10.0, mu_g=0.1, sigma_t=1.96, g=0.98)
+    ax = torch.arange(n, dtype=torch.float64, device="cuda") * h
+    z, y, x = torch.meshgrid(ax, ax, ax, indexing="ij")
+
+    def fld(vals):
+        f = nn4.field(Gv)
+        nn4.nodes(f, Gv).copy_(vals)
+        return f
+
+    r = torch.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.3) ** 2)
+    C = fld(torch.clamp(0.5 + (r - 0.25) / (2 * h), 0.0, 1.0))
+    bump = torch.sin(math.pi * x) * torch.sin(math.pi * y) * torch.sin(math.pi * z)
+    U = [fld(0.1 * bump * torch.cos(math.pi * (x + c * y))) for c in (0.0, 0.5, 1.0)]
+    P = fld(1000.0 * 0.98 * (1.0 - z))
+    del r, bump, x, y, z
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        ts = []
+        for _ in range(max(1, args.steps)):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    sC, Cn, ws = torch.empty_like(C), torch.empty_like(C), nn4.vof_workspace(Gc)
+    src, _ = nn4.momentum_sources(Gv, fp, C)
+    uh = [u.clone() for u in U]
+    dp, pnh = fld(torch.zeros((n, n, n), dtype=torch.float64, device="cuda")), nn4.field(Gv)
+    mass = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ms = {
+        "vof_advect_residual": timed(lambda: nn4.vof_advect_residual(Gc, C, U[0], U[1], U[2], 1e-4, sC, Cn, ws)),
+        "momentum_sources": timed(lambda: nn4.momentum_sources(Gv, fp, C)),
+        "momentum_predict": timed(lambda: nn4.momentum_predict(Gv, fp, C, U, uh, P, src)),
+        "pressure_rhs_hs": timed(lambda: nn4.pressure_rhs_hs(Gp, src)),
+        "pressure_rhs_nh": timed(lambda: nn4.pressure_rhs_nh(Gp, fp, C, U)),
+        "velocity_correct": timed(lambda: nn4.velocity_correct(Gv, fp, C, dp, uh, pnh)),
+        "mass_sum": timed(lambda: nn4.mass_sum(Gc, C, mass)),
+    }
+    hbm = _load_peaks()["hbm_gbs"]
+    res = {}
+    for k, t in ms.items():
+        gbs = FLOW_BYTES[k] * n ** 3 / (t * 1e-3) / 1e9
+        res[k] = {"ms": t, "compulsory_bytes_per_node": FLOW_BYTES[k], "gbs": gbs, "frac_hbm": gbs / hbm}
+    print(json.dumps({"metric": "flow_entry_ms", "unit": "ms", "n": n, "steps": args.steps, "warmup": args.warmup,
+                      "dtype": "f64", "results": res}), flush=True)
 
 
 # ---------------------------------------------------------------- batching form and time step
