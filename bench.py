@@ -418,6 +418,12 @@ def main():
                "f64": run_batched(nn4, torch, nn4.F64, 1, 1, 1)}
     batched["speedup_vs_fp64"] = batched["mixed"]["solves_per_s"] / batched["f64"]["solves_per_s"]
     column = run_column_steps(nn4, torch)
+    try:  # the explicit terms at configuration 5's size; reported, never fatal to the line
+        flow = {"n": 513, "steps": 3, "warmup": 1, "dtype": "f64",
+                "results": flow_kernel_times(nn4, torch, 513, 3, 1)}
+    except Exception as ex:
+        flow = {"failed": str(ex)[:300]}
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -441,7 +447,7 @@ def main():
             "roofline": roof, "roofline_kernels": roof_all,
             "kernel_shares": {kk: round(vv[1] / total_prof, 4) for kk, vv in
                               sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]},
-            "batched": batched, "column_step": column,
+            "batched": batched, "column_step": column, "flow_kernels": flow,
             "cpu_baseline": cpu,
             "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
                     "d2h_bytes_per_step": nbytes},
@@ -524,6 +530,15 @@ FLOW_BYTES = {"vof_advect_residual": 48,   # C, u, v, w read; s_C, C_next writte
 
 
 def run_flow_kernels(args):
+    """--flow-kernels: one JSON line with flow_kernel_times at n = --flow-n."""
+    import torch
+    from paper_2401_06755_gb300 import nn4
+    res = flow_kernel_times(nn4, torch, args.flow_n, args.steps, args.warmup)
+    print(json.dumps({"metric": "flow_entry_ms", "unit": "ms", "n": args.flow_n, "steps": args.steps,
+                      "warmup": args.warmup, "dtype": "f64", "results": res}), flush=True)
+
+
+def flow_kernel_times(nn4, torch, n, steps, warmup):
     """Device time of each explicit multiphase entry point (FP64) on the rising-bubble grid of
     n^3 nodes on the unit cube (bubble radius 0.25 at (0.5, 0.5, 0.3), ramp 2h, densities
     1000/1, viscosities 10/0.1, sigma 1.96, g 0.98, dt 1e-4), velocities a smooth field that
@@ -532,9 +547,6 @@ def run_flow_kernels(args):
     compulsory bytes of FLOW_BYTES against the measured copy bandwidth; the volume-fraction and
     momentum steps are FP64-arithmetic-bound, so their fraction is low by design."""
     import math
-    import torch
-    from paper_2401_06755_gb300 import nn4
-    n = args.flow_n
     h = 1.0 / (n - 1)
     Gv = nn4.Grid((n, n, n), (h, h, h), (nn4.DIRICHLET,) * 6)
     Gc = nn4.Grid((n, n, n), (h, h, h))
@@ -557,10 +569,10 @@ def run_flow_kernels(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed(fn):
-        for _ in range(max(1, args.warmup)):
+        for _ in range(max(1, warmup)):
             fn()
         ts = []
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, steps)):
             e0.record()
             fn()
             e1.record()
@@ -587,8 +599,7 @@ def run_flow_kernels(args):
     for k, t in ms.items():
         gbs = FLOW_BYTES[k] * n ** 3 / (t * 1e-3) / 1e9
         res[k] = {"ms": t, "compulsory_bytes_per_node": FLOW_BYTES[k], "gbs": gbs, "frac_hbm": gbs / hbm}
-    print(json.dumps({"metric": "flow_entry_ms", "unit": "ms", "n": n, "steps": args.steps, "warmup": args.warmup,
-                      "dtype": "f64", "results": res}), flush=True)
+    return res
 
 
 # ---------------------------------------------------------------- batching form and time step
