@@ -17,9 +17,9 @@ Readings where the paper is silent (see also the module docstring of ``mg``):
   * "w_m / m_l - E" in Eq. a_psi divides by the lumped nodal volume m_i.
 Parity status: the mass sum is pinned by exact quadrature identities; the VOF step is pinned by
 the invariants in tests/test_oracle_flow.py (uniform field, linear profile weights, 1D-invariant
-advection, mass conservation in a divergence-free flow, the printed constants) and is otherwise
-"parity unpinned" (no printed example).  The momentum predictor is pinned by the exact advection
-of a linear velocity field and by the hydrostatic rest state; the surface tension by a plane
+advection, mass conservation in a divergence-free flow, mirror and axis-exchange symmetry, the
+printed constants) and is otherwise "parity unpinned" (no printed example).  The momentum predictor is pinned by the exact advection
+of a linear velocity field, by mirror symmetry and by the hydrostatic rest state; the surface tension by a plane
 interface (no force) and by the curvature 2/r of a sphere; the pressure right-hand sides and the
 velocity correction by the hydrostatic column, a divergence-free uniform-density field and a
 linear pressure.
