@@ -15,14 +15,18 @@ Readings where the paper is silent (see also the module docstring of ``mg``):
     k_abs), clamped to [-k_min, k_max]; the oscillation detector uses the copy-halo of Section
     2.3.3 at walls (so S = 0 there) and the linear (3x3x3) form.
   * "w_m / m_l - E" in Eq. a_psi divides by the lumped nodal volume m_i.
-Parity status: the mass sum is pinned by exact quadrature identities; the VOF step is pinned by
-the invariants in tests/test_oracle_flow.py (uniform field, linear profile weights, 1D-invariant
+Parity status: the mass sum is pinned by exact quadrature identities.  The VOF step is pinned
+by closed forms of every intermediate (gradient, a_C, k_abs, detectors with the override, w+ and
+w-, u*, k^-, the clamped k^d) on a separable cubic field with anisotropic spacing, derived by
+Taylor expansion, and by invariants (uniform field, linear profile weights, 1D-invariant
 advection, mass conservation in a divergence-free flow, mirror and axis-exchange symmetry, the
-printed constants) and is otherwise "parity unpinned" (no printed example).  The momentum predictor is pinned by the exact advection
-of a linear velocity field, by mirror symmetry and by the hydrostatic rest state; the surface tension by a plane
-interface (no force) and by the curvature 2/r of a sphere; the pressure right-hand sides and the
-velocity correction by the hydrostatic column, a divergence-free uniform-density field and a
-linear pressure.
+printed constants).  The momentum predictor is pinned by closed forms of a, k_abs, k_square,
+k_max and k_Psi (each branch of the min reached), the exact advection of a linear velocity
+field, mirror symmetry and the hydrostatic rest state; the surface tension by a plane interface
+(no force) and by the curvature 2/r of a sphere; the pressure right-hand sides and the velocity
+correction by the hydrostatic column, a divergence-free uniform-density field and a linear
+pressure.  tests/test_oracle_flow.py plants nineteen slips in a copy of this module and checks
+that each one fails a pin.
 """
 
 from dataclasses import dataclass
@@ -221,13 +225,15 @@ def velocity_correction(shape, h, rho, dp, dt, wall_mask=None):
     return out
 
 
-def momentum_predict(shape, h, C, un, uh, p_total, dt, prm, wall_mask=None):
+def momentum_predict(shape, h, C, un, uh, p_total, dt, prm, wall_mask=None, parts=None):
     """One Stage-2 iteration (Eqs. Petrov-u/v/w, k_Psi-n, k-abs, k-square, max-k, velocity-1).
 
     un: velocity at level n; uh: the current u^{n+1/2}; p_total = p_hs + p_nh.  For each component
     Psi:  s~ = rho (u.grad_raw Psi) + f^lap(Psi, k_Psi; w_lap) + f(p; w_d) - f(s_Psi + s_tPsi; w_m),
     with k_Psi = rho min(k_max, k_abs, k_square) + mu computed from u^{n+1/2} (reading), then
     Psi~ = Psi^n - dt s~ / (m rho) (sigma = 0).  Returns (u~, u^{n+1/2} = (u^n + u~) / 2).
+    If ``parts`` is a dict it receives the per-component intermediate fields (lists over the
+    component c): "a" (Eq. a_psi), "k_abs", "k_square", "k" (Eq. k_Psi-n) and "k_max" (Eq. max-k).
     """
     ei, m = _filters(shape, h)
     rho = density(C, prm)
@@ -237,6 +243,7 @@ def momentum_predict(shape, h, C, un, uh, p_total, dt, prm, wall_mask=None):
     L = ei["stiff"]
     kmax = h[0] * np.abs(uh[0]) + h[1] * np.abs(uh[1]) + h[2] * np.abs(uh[2])   # Eq. max-k
     ut = []
+    rec = {"a": [], "k_abs": [], "k_square": [], "k": [], "k_max": kmax}
     for c in range(3):
         psi = uh[c]
         raw = [fem.apply_assembled(ei["grad"][d], psi) for d in range(3)]
@@ -252,6 +259,8 @@ def momentum_predict(shape, h, C, un, uh, p_total, dt, prm, wall_mask=None):
                 (prm.eps_k + (np.abs(uh[0] * pd[0]) + np.abs(uh[1] * pd[1]) + np.abs(uh[2] * pd[2]))
                  * (pd[0] ** 2 + pd[1] ** 2 + pd[2] ** 2) / 3.0))                   # Eq. k-square
         k = rho * np.minimum(kmax, np.minimum(k_abs, k_sq)) + mu                     # Eq. k_Psi-n
+        for key, val in (("a", a), ("k_abs", k_abs), ("k_square", k_sq), ("k", k)):
+            rec[key].append(val)
         s = rho * (uh[0] * raw[0] + uh[1] * raw[1] + uh[2] * raw[2])
         s = s + 0.5 * (fem.apply_assembled(L, k * psi) + k * fem.apply_assembled(L, psi)
                        - psi * fem.apply_assembled(L, k))                            # Eq. k-T
@@ -261,4 +270,6 @@ def momentum_predict(shape, h, C, un, uh, p_total, dt, prm, wall_mask=None):
         if wall_mask is not None:
             u_new = np.where(wall_mask, 0.0, u_new)
         ut.append(u_new)
+    if parts is not None:
+        parts.update(rec)
     return ut, [0.5 * (un[c] + ut[c]) for c in range(3)]

@@ -1,8 +1,10 @@
 """Pins of the oracle's explicit flow terms: printed constants, exact quadrature, invariants."""
 
 import os
+import sys
 
 import numpy as np
+import pytest
 
 from oracle import fem, flow
 from synth import node_coords, sphere_ramp_field
@@ -268,3 +270,296 @@ def test_momentum_predictor_is_mirror_symmetric():
     back = [-f(utm[0]), f(utm[1]), f(utm[2])]
     for c in range(3):
         assert np.abs(back[c] - ut[c]).max() <= 1e-12 * max(np.abs(a).max() for a in ut), c
+
+
+# ------------------------------------------------ closed-form Petrov-Galerkin coefficient pins
+#
+# On a separable cubic field C = P(x) + Q(y) + R(z) every coefficient of the compressive scheme
+# has a closed form at nodes two or more away from every face, derived here by Taylor expansion
+# instead of by applying the assembled filters:
+#   * the pointwise gradient m^-1 f(C; w_x) is the central difference (P_{i+1} - P_{i-1}) / 2h_x
+#     (the y and z mass factors of w_x = G (x) M (x) M sum to the lumped volume), which for a cubic
+#     is P'(x) + p3 h_x^2;
+#   * with a uniform velocity, g = u.grad C is quadratic along each axis, and the consistent mass
+#     over the lumped mass minus the identity acts on a quadratic as (g_{i-1} + 4 g_i + g_{i+1})/6
+#     - g_i = h^2 g'' / 6, so a_C = alpha_a (u p3 h_x^2 + v q3 h_y^2 + w r3 h_z^2), a constant.
+# The coefficients that follow are evaluated from these inputs with the printed constants of
+# tests/golden/vof_constants.txt, one equation at a time, for three time steps: one that leaves
+# every coefficient inside [-k_min, k_max], one that clamps about half of the positive ones at
+# k_max and one that clamps about half of the negative ones at -k_min.
+
+
+def _printed():
+    out = {}
+    for line in open(os.path.join(GOLDEN, "vof_constants.txt")):
+        if line.strip() and not line.startswith("#"):
+            name, value = line.split()[:2]
+            out[name] = float(value)
+    return out
+
+
+def _cubic(c, x0):
+    """P(t) = c0 + c1 s + c2 s^2 + c3 s^3 with s = t - x0, and P'(t)."""
+    return (lambda t: c[0] + c[1] * (t - x0) + c[2] * (t - x0) ** 2 + c[3] * (t - x0) ** 3,
+            lambda t: c[1] + 2 * c[2] * (t - x0) + 3 * c[3] * (t - x0) ** 2)
+
+
+_VOF_N, _VOF_H = (11, 13, 9), (0.1, 0.05, 0.08)              # anisotropic spacing
+_VOF_CUBICS = (((0.45, -0.3, 0.0, 25.0), 0.5),               # P: an extremum inside (S^x < 0)
+               ((0.0, 0.9, 1.0, -8.0), 0.3),                 # Q
+               ((0.0, 0.4, 0.0, 3.0), 0.32))                 # R
+_VOF_VEL = (0.7, -0.4, 0.25)
+_INNER = (slice(2, -2),) * 3
+
+
+def _vof_closed_form(dt):
+    """Returns (C, velocity fields, expected parts on the inner nodes) for the separable cubic."""
+    K = _printed()
+    h = _VOF_H
+    X = node_coords(_VOF_N, h)
+    fs = [_cubic(*c) for c in _VOF_CUBICS]
+    C = sum(fs[d][0](X[d]) for d in range(3))
+    # Taylor: central difference of a cubic, and the mixed-mass residual of a quadratic
+    grad = [fs[d][1](X[d]) + _VOF_CUBICS[d][0][3] * h[d] ** 2 for d in range(3)]
+    a = K["alpha_a"] * sum(_VOF_VEL[d] * _VOF_CUBICS[d][0][3] * h[d] ** 2 for d in range(3))
+    a = np.full(C.shape, a)
+    # Eq. efficient-kabs (general spacing)
+    sabs = sum(np.abs(g) for g in grad)
+    k_abs = K["alpha_kabs"] * np.abs(a) * sum(h[d] * np.abs(grad[d]) for d in range(3)) \
+        / (K["eps_k"] + sabs * sabs / 3)
+    # Eqs. Sx-lin..Sz-lin on nodal values, then the 0.95 / 0.05 override (S = -1)
+    S = []
+    for d in range(3):
+        P = fs[d][0]
+        t = X[d]
+        raw = (P(t) - P(t - h[d])) * (P(t + h[d]) - P(t))
+        S.append(np.where((C > K["detect_hi"]) | (C < K["detect_lo"]), -1.0, raw))
+    w_plus = [np.clip(-K["K_plus"] * s, 0.0, 1.0) for s in S]      # -max(-1, min(0, K+ S))
+    w_minus = [np.clip(K["K_minus"] * s, 0.0, 1.0) for s in S]     # min(1, max(0, K- S))
+    # Eqs. normalisation and negativek
+    g2 = sum(g * g for g in grad)
+    proj = sum(_VOF_VEL[d] * grad[d] for d in range(3)) / (K["eps_x"] + g2)
+    ustar_abs = sum(np.abs(grad[d] * proj) for d in range(3))
+    speed2 = sum(v * v for v in _VOF_VEL)
+    k_neg = -K["beta"] * speed2 / (K["eps_x"] + g2 * ustar_abs / 3)
+    # Eq. positivek, the directional combination, and the clamp of Eq. alpha_min_and_max
+    k_lo = K["alpha_min"] * max(h) ** 2 / dt
+    k_hi = K["alpha_max"] * min(h) ** 2 / dt
+    k = [np.clip(w_plus[d] * K["K_pos"] * k_abs + w_minus[d] * k_neg / h[d], -k_lo, k_hi)
+         for d in range(3)]
+    vel = [np.full(C.shape, v) for v in _VOF_VEL]
+    expect = {"grad": grad, "a_C": a, "k_abs": k_abs, "S": S, "w_plus": w_plus,
+              "w_minus": w_minus, "k_neg": k_neg, "k": k}
+    return C, vel, {key: ([f[_INNER] for f in val] if isinstance(val, list) else val[_INNER])
+                    for key, val in expect.items()}
+
+
+def _close(got, want, rel=1e-12, floor=1e-300):
+    return np.all(np.abs(got - want) <= rel * np.abs(want) + floor)
+
+
+# dt = 1e-11: no clamp; 0.05: k_max clamps part of the positive side; 3.5e-6: -k_min part of the
+# negative side (the spreads are checked in test_closed_form_cases_reach_every_branch)
+_VOF_DTS = (1e-11, 0.05, 3.5e-6)
+
+
+def test_vof_coefficients_match_closed_form():
+    """Every intermediate of the compressive Petrov-Galerkin step (Sections 2.3.5-2.3.6) equals
+    its closed form on a separable cubic field with anisotropic spacing."""
+    for dt in _VOF_DTS:
+        C, vel, want = _vof_closed_form(dt)
+        _, _, parts = flow.vof_step(C.shape, _VOF_H, C, *vel, dt)
+        for key, val in want.items():
+            got = parts[key]
+            if isinstance(val, list):
+                for d in range(3):
+                    assert _close(got[d][_INNER], val[d], floor=1e-15 if key == "grad" else 1e-300), (dt, key, d)
+            else:
+                assert _close(got[_INNER], val), (dt, key)
+
+
+def test_closed_form_cases_reach_every_branch():
+    """The closed-form cases exercise each branch of the scheme at some inner nodes: the detector
+    override, S < 0 with a fractional w+, S > 0 with a fractional w-, and both clamps partly
+    active, so a slip in any of them changes the pinned values."""
+    K = _printed()
+    C, _, want = _vof_closed_form(_VOF_DTS[0])
+    Ci = C[_INNER]
+    assert ((Ci > K["detect_hi"]) | (Ci < K["detect_lo"])).sum() > 10
+    assert any(((want["w_plus"][d] > 0) & (want["w_plus"][d] < 1)).sum() > 10 for d in range(3))
+    assert any(((want["w_minus"][d] > 0) & (want["w_minus"][d] < 1)).sum() > 10 for d in range(3))
+    for i, dt in enumerate(_VOF_DTS):
+        _, _, want = _vof_closed_form(dt)
+        hi = K["alpha_max"] * min(_VOF_H) ** 2 / dt
+        lo = K["alpha_min"] * max(_VOF_H) ** 2 / dt
+        at_hi = sum((k == hi).sum() for k in want["k"])
+        at_lo = sum((k == -lo).sum() for k in want["k"])
+        free_pos = sum(((k > 0) & (k < hi)).sum() for k in want["k"])
+        free_neg = sum(((k < 0) & (k > -lo)).sum() for k in want["k"])
+        if i == 0:
+            assert at_hi == 0 and at_lo == 0 and free_pos > 100 and free_neg > 100
+        elif i == 1:
+            assert at_hi > 50 and free_pos > 50
+        else:
+            assert at_lo > 50 and free_neg > 50
+
+
+def test_vof_update_with_uniform_clamped_diffusion_matches_closed_form():
+    """Eqs. Petrov-Cs and transport-indicator-1 in closed form.  C = 0.97 + a separable cubic of
+    small amplitude lies in the override band (C > 0.95), so w+ = 1 and w- = 0 in every
+    direction; with dt = 10 every 3 k_abs exceeds k_max, so k^d = k_max uniformly.  The
+    Petrov-Galerkin term 0.5[D(kC) + k DC - C Dk] is then k_max D_d C, and on a cubic
+    D_d C = -m P_d'' (the 1D stiffness row times the y, z masses), while f(C; w_d) = m times the
+    central difference P_d' + p3 h_d^2.  So s_C = m [sum_d u_d (P_d' + p3 h_d^2) - k_max sum_d P_d'']
+    and C^{n+1} = C - dt s_C / m at nodes two or more from every face."""
+    K = _printed()
+    n, h, dt = (9, 11, 9), (0.1, 0.05, 0.08), 10.0
+    X = node_coords(n, h)
+    cub = [(0.002, 0.3, 0.5), (0.001, 0.2, 0.4), (0.0015, 0.1, 0.3)]   # amplitude, c1, c3 about 0.3
+    C = 0.97 + sum(A * (c1 * (X[d] - 0.3) + c3 * (X[d] - 0.3) ** 3) for d, (A, c1, c3) in enumerate(cub))
+    vel = (0.7, -0.4, 0.25)
+    s, Cn, parts = flow.vof_step(C.shape, h, C, *[np.full(C.shape, v) for v in vel], dt)
+    k_hi = K["alpha_max"] * min(h) ** 2 / dt
+    ring = (slice(1, -1),) * 3
+    assert all(np.all(parts["k"][d][ring] == k_hi) for d in range(3))
+    m = h[0] * h[1] * h[2]
+    d1 = [A * (c1 + 3 * c3 * (X[d] - 0.3) ** 2 + c3 * h[d] ** 2) for d, (A, c1, c3) in enumerate(cub)]
+    d2 = [A * 6 * c3 * (X[d] - 0.3) for d, (A, c1, c3) in enumerate(cub)]
+    s_want = m * (sum(vel[d] * d1[d] for d in range(3)) - k_hi * sum(d2))
+    assert np.abs(s[_INNER] - s_want[_INNER]).max() <= 1e-12 * np.abs(s_want).max()
+    assert np.abs(Cn[_INNER] - (C - dt * s_want / m)[_INNER]).max() <= 1e-12
+
+
+# Momentum (Stage 2): u = P(y) cubic, v and w uniform, uniform C.  For the u component only
+# d/dy is non-zero, g = v P~'(y) is quadratic and a = alpha_a v p3 h_y^2; the v and w components
+# are uniform, so their a, k_abs and k_square vanish and k_Psi = mu.  The cubic is chosen so that
+# k_max, k_abs and k_square are each the smallest of the three at some inner nodes.
+_MOM_N, _MOM_H = (9, 17, 9), (0.1, 0.05, 0.08)
+_MOM_P3 = 100.0
+_MOM_CUBIC = ((0.0, -0.9 * _MOM_P3 * 0.05 ** 2, 0.0, _MOM_P3), 0.4)
+_MOM_VW = (0.03, -0.02)
+_MOM_C = 0.4
+
+
+def _momentum_closed_form():
+    K = _printed()
+    prm = flow.FlowParams()
+    h = _MOM_H
+    x, y, z = node_coords(_MOM_N, h)
+    P, dP = _cubic(*_MOM_CUBIC)
+    uh = [P(y), np.full(y.shape, _MOM_VW[0]), np.full(y.shape, _MOM_VW[1])]
+    C = np.full(y.shape, _MOM_C)
+    rho = prm.rho_l * _MOM_C + prm.rho_g * (1 - _MOM_C)              # Eq. density-n
+    mu = prm.mu_l * _MOM_C + prm.mu_g * (1 - _MOM_C)
+    py = dP(y) + _MOM_CUBIC[0][3] * h[1] ** 2                        # central difference of a cubic
+    a = K["alpha_a"] * _MOM_VW[0] * _MOM_CUBIC[0][3] * h[1] ** 2
+    k_max = h[0] * np.abs(uh[0]) + h[1] * abs(_MOM_VW[0]) + h[2] * abs(_MOM_VW[1])   # Eq. max-k
+    k_abs = K["alpha_kabs"] * abs(a) * h[1] * np.abs(py) / (K["eps_k"] + py * py / 3)  # efficient-kabs
+    h_psi = h[1] * np.abs(py) / (K["eps_k"] + np.abs(py))                               # Eq. h_Psi
+    k_sq = K["alpha_ksquare"] * a * a * h_psi / (K["eps_k"] + np.abs(_MOM_VW[0] * py) * py * py / 3)
+    k_u = rho * np.minimum(k_max, np.minimum(k_abs, k_sq)) + mu                         # Eq. k_Psi-n
+    want = {"a": [np.full(y.shape, a), 0 * y, 0 * y], "k_abs": [k_abs, 0 * y, 0 * y],
+            "k_square": [k_sq, 0 * y, 0 * y], "k": [k_u, mu + 0 * y, mu + 0 * y]}
+    return C, uh, prm, k_max, {key: [f[_INNER] for f in val] for key, val in want.items()}
+
+
+def test_momentum_diffusivity_matches_closed_form():
+    """k_Psi of Eq. k_Psi-n (with Eqs. a_psi, efficient-kabs, h_Psi, k-square, max-k) for each
+    velocity component equals its closed form; rho and mu are not 1 and 0."""
+    C, uh, prm, k_max, want = _momentum_closed_form()
+    parts = {}
+    flow.momentum_predict(C.shape, _MOM_H, C, uh, uh, np.zeros(C.shape), 1e-4, prm, parts=parts)
+    assert _close(parts["k_max"][_INNER], k_max[_INNER])
+    for key, val in want.items():
+        for c in range(3):
+            assert _close(parts[key][c][_INNER], val[c], floor=1e-18), (key, c)
+
+
+def test_momentum_closed_form_reaches_every_branch_of_the_min():
+    _, _, _, k_max, want = _momentum_closed_form()
+    which = np.argmin(np.stack([k_max[_INNER], want["k_abs"][0], want["k_square"][0]]), axis=0)
+    assert all((which == i).sum() >= 10 for i in range(3))
+
+
+# ------------------------------------------------ the pins catch plausible slips in the oracle
+
+_SLIPS = {
+    # Eq. efficient-kabs: the special-case denominator (sum |grad|) instead of its square
+    "kabs_denominator": ("/ (prm.eps_k + sum_abs ** 2 / 3.0))", "/ (prm.eps_k + sum_abs / 3.0))"),
+    # Eq. positivek: K = 1 instead of 3
+    "positive_factor": ("k_plus = prm.K_pos * k_abs", "k_plus = k_abs"),
+    # Eq. negativek: the /3 of the denominator dropped
+    "negk_third": ("+ np.abs(ustar[2])) / 3.0)", "+ np.abs(ustar[2])))"),
+    # k^{d-} = k^- / Delta d: the division dropped
+    "negk_spacing": ("k_minus = k_neg / h[d]", "k_minus = k_neg"),
+    # Eq. alpha_min_and_max: k_max from the largest spacing
+    "kmax_spacing": ("k_max = prm.alpha_max * min(h) ** 2 / dt", "k_max = prm.alpha_max * max(h) ** 2 / dt"),
+    # ... and k_min from the smallest
+    "kmin_spacing": ("k_min = prm.alpha_min * max(h) ** 2 / dt", "k_min = prm.alpha_min * min(h) ** 2 / dt"),
+    # Eq. a_psi: alpha_a = 1
+    "alpha_a": ("a_C = prm.alpha_a * (", "a_C = 1.0 * ("),
+    # the 0.95 / 0.05 detector override removed, or only its upper half kept
+    "override": ("S.append(np.where(over, -1.0, s))", "S.append(s)"),
+    "override_lo": ("over = (C > prm.detect_hi) | (C < prm.detect_lo)", "over = (C > prm.detect_hi)"),
+    # the weights: w+ with the wrong sign, K- dropped from w-
+    "w_plus_sign": ("w_plus = [-np.maximum(", "w_plus = [np.maximum("),
+    "w_minus_gain": ("np.maximum(0.0, prm.K_minus * s))", "np.maximum(0.0, s))"),
+    # Eq. normalisation without its denominator
+    "ustar_norm": ("/ (prm.eps_x + gradsq)\n", "\n"),
+    # Eq. k-square with alpha_kabs, or without its /3
+    "alpha_ksquare": ("k_sq = (prm.alpha_ksquare * a * a", "k_sq = (prm.alpha_kabs * a * a"),
+    "ksq_third": ("* (pd[0] ** 2 + pd[1] ** 2 + pd[2] ** 2) / 3.0))", "* (pd[0] ** 2 + pd[1] ** 2 + pd[2] ** 2)))"),
+    # Eq. h_Psi with the squared sum
+    "h_psi": ("h_psi = hsum / (prm.eps_k + sab)", "h_psi = hsum / (prm.eps_k + sab ** 2)"),
+    # Eq. max-k without the spacings
+    "kmax_field": ("kmax = h[0] * np.abs(uh[0]) + h[1] * np.abs(uh[1]) + h[2] * np.abs(uh[2])",
+                   "kmax = np.abs(uh[0]) + np.abs(uh[1]) + np.abs(uh[2])"),
+    # Eq. Petrov-Cs: the C Dk term with the wrong sign; Eq. transport-indicator-1 without m
+    "pg_sign": ("- C * fem.apply_assembled(D, kd[d]))", "+ C * fem.apply_assembled(D, kd[d]))"),
+    "update_mass": ("C_next = C - dt * s_C / m", "C_next = C - dt * s_C"),
+    # Eq. k_Psi-n: rho dropped, k_abs dropped from the min, mu dropped
+    "kpsi_rho": ("k = rho * np.minimum(kmax, np.minimum(k_abs, k_sq)) + mu",
+                 "k = np.minimum(kmax, np.minimum(k_abs, k_sq)) + mu"),
+    "kpsi_kabs": ("k = rho * np.minimum(kmax, np.minimum(k_abs, k_sq)) + mu",
+                  "k = rho * np.minimum(kmax, k_sq) + mu"),
+    "kpsi_mu": ("k = rho * np.minimum(kmax, np.minimum(k_abs, k_sq)) + mu",
+                "k = rho * np.minimum(kmax, np.minimum(k_abs, k_sq))"),
+}
+
+
+def _mutant(old, new):
+    """A copy of oracle.flow with one source substitution (the slip is planted in the oracle, on
+    the CPU; the product path is not involved)."""
+    import importlib.util
+    import types
+    src_path = flow.__file__
+    src = open(src_path).read()
+    assert src.count(old) == 1, old
+    mod = types.ModuleType("oracle._flow_mutant")
+    mod.__package__ = "oracle"
+    mod.__file__ = src_path
+    exec(compile(src.replace(old, new), src_path, "exec"), mod.__dict__)
+    assert importlib.util.find_spec("oracle") is not None
+    return mod
+
+
+_PINS = ("test_uniform_field_stays_uniform", "test_mass_conserved_in_divergence_free_wall_tangent_flow",
+         "test_vof_update_with_uniform_clamped_diffusion_matches_closed_form", "test_linear_profile_has_no_positive_weight",
+         "test_invariant_direction_advection_leaves_interior_unchanged",
+         "test_momentum_predictor_advects_a_linear_field_exactly",
+         "test_vof_coefficients_match_closed_form", "test_momentum_diffusivity_matches_closed_form")
+
+
+@pytest.mark.parametrize("slip", sorted(_SLIPS))
+def test_pins_catch_planted_mistakes(monkeypatch, slip):
+    """Each plausible slip in the coefficient chains, planted in a copy of the oracle, makes at
+    least one pin fail."""
+    mod = _mutant(*_SLIPS[slip])
+    monkeypatch.setattr(sys.modules[__name__], "flow", mod)
+    failed = []
+    for name in _PINS:
+        try:
+            globals()[name]()
+        except AssertionError:
+            failed.append(name)
+    assert failed, slip
