@@ -522,9 +522,9 @@ def run_residual_restrict(args):
 # compulsory bytes per node of each entry point: every input field read once, every output written once
 FLOW_BYTES = {"vof_advect_residual": 48,   # C, u, v, w read; s_C, C_next written
               "momentum_sources": 40,      # C read; s_x, s_y, s_z, kappa written
-              "momentum_predict": 136,     # C, u^n, u^{n+1/2}, p, s read; u~ written; u^{n+1/2} rewritten
+              "momentum_predict": 136,     # C, u^n, u^{n+1/2}, p, s read; u~ and the next u^{n+1/2} written
               "pressure_rhs_hs": 32,       # s read; b written
-              "pressure_rhs_nh": 48,       # C, u~ read; b, rho written
+              "pressure_rhs_nh": 40,       # C, u~ read; b written
               "velocity_correct": 80,      # C, dp read; u read and written; p_nh read and written
               "mass_sum": 8}               # C read
 
@@ -535,17 +535,18 @@ def run_flow_kernels(args):
     from paper_2401_06755_gb300 import nn4
     res = flow_kernel_times(nn4, torch, args.flow_n, args.steps, args.warmup)
     print(json.dumps({"metric": "flow_entry_ms", "unit": "ms", "n": args.flow_n, "steps": args.steps,
-                      "warmup": args.warmup, "dtype": "f64", "results": res}), flush=True)
+                      "warmup": args.warmup, "results": res}), flush=True)
 
 
-def flow_kernel_times(nn4, torch, n, steps, warmup):
-    """Device time of each explicit multiphase entry point (FP64) on the rising-bubble grid of
+def flow_kernel_times(nn4, torch, n, steps, warmup, computes=("f64", "f32")):
+    """Device time of each explicit multiphase entry point, per arithmetic form (FP64, and FP32 on
+    FP64 state), on the rising-bubble grid of
     n^3 nodes on the unit cube (bubble radius 0.25 at (0.5, 0.5, 0.3), ramp 2h, densities
     1000/1, viscosities 10/0.1, sigma 1.96, g 0.98, dt 1e-4), velocities a smooth field that
     vanishes on the no-slip walls.  Each figure is the median of `steps` launches after `warmup`;
     the fields (1 GB each at 513^3) are far larger than L2.  Bandwidth is counted from the
-    compulsory bytes of FLOW_BYTES against the measured copy bandwidth; the volume-fraction and
-    momentum steps are FP64-arithmetic-bound, so their fraction is low by design."""
+    compulsory bytes of FLOW_BYTES against the measured copy bandwidth (the FP64 forms are bound
+    by the FP64 pipe, so their fraction of HBM is low by design)."""
     import math
     h = 1.0 / (n - 1)
     Gv = nn4.Grid((n, n, n), (h, h, h), (nn4.DIRICHLET,) * 6)
@@ -581,24 +582,34 @@ def flow_kernel_times(nn4, torch, n, steps, warmup):
         return statistics.median(ts)
 
     sC, Cn, ws = torch.empty_like(C), torch.empty_like(C), nn4.vof_workspace(Gc)
-    src, _ = nn4.momentum_sources(Gv, fp, C)
+    mws = nn4.momentum_workspace(Gv)
+    ut, uhn = [torch.empty_like(C) for _ in range(3)], [torch.empty_like(C) for _ in range(3)]
     uh = [u.clone() for u in U]
     dp, pnh = fld(torch.zeros((n, n, n), dtype=torch.float64, device="cuda")), nn4.field(Gv)
     mass = torch.zeros(1, dtype=torch.float64, device="cuda")
-    ms = {
-        "vof_advect_residual": timed(lambda: nn4.vof_advect_residual(Gc, C, U[0], U[1], U[2], 1e-4, sC, Cn, ws)),
-        "momentum_sources": timed(lambda: nn4.momentum_sources(Gv, fp, C)),
-        "momentum_predict": timed(lambda: nn4.momentum_predict(Gv, fp, C, U, uh, P, src)),
-        "pressure_rhs_hs": timed(lambda: nn4.pressure_rhs_hs(Gp, src)),
-        "pressure_rhs_nh": timed(lambda: nn4.pressure_rhs_nh(Gp, fp, C, U)),
-        "velocity_correct": timed(lambda: nn4.velocity_correct(Gv, fp, C, dp, uh, pnh)),
-        "mass_sum": timed(lambda: nn4.mass_sum(Gc, C, mass)),
-    }
     hbm = _load_peaks()["hbm_gbs"]
     res = {}
-    for k, t in ms.items():
-        gbs = FLOW_BYTES[k] * n ** 3 / (t * 1e-3) / 1e9
-        res[k] = {"ms": t, "compulsory_bytes_per_node": FLOW_BYTES[k], "gbs": gbs, "frac_hbm": gbs / hbm}
+    for cname in computes:
+        cm = nn4.F64 if cname == "f64" else nn4.F32
+        fpc = nn4.flow_params(1e-4, compute=cm, rho_l=1000.0, rho_g=1.0, mu_l=10.0, mu_g=0.1, sigma_t=1.96, g=0.98)
+        vp = nn4.vof_params(1e-4, cm)
+        src, _ = nn4.momentum_sources(Gv, fpc, C)
+        ms = {
+            "vof_advect_residual": timed(lambda: nn4.vof_advect_residual(Gc, C, U[0], U[1], U[2], 1e-4, sC, Cn, ws,
+                                                                         params=vp)),
+            "momentum_sources": timed(lambda: nn4.momentum_sources(Gv, fpc, C)),
+            "momentum_predict": timed(lambda: nn4.momentum_predict(Gv, fpc, C, U, uh, P, src, ut, uhn, mws)),
+            "pressure_rhs_hs": timed(lambda: nn4.pressure_rhs_hs(Gp, src, compute=cm)),
+            "pressure_rhs_nh": timed(lambda: nn4.pressure_rhs_nh(Gp, fpc, C, U)),
+            "velocity_correct": timed(lambda: nn4.velocity_correct(Gv, fpc, C, dp, uh, pnh)),
+            "mass_sum": timed(lambda: nn4.mass_sum(Gc, C, mass)),
+        }
+        del src
+        out = {}
+        for k, t in ms.items():
+            gbs = FLOW_BYTES[k] * n ** 3 / (t * 1e-3) / 1e9
+            out[k] = {"ms": t, "compulsory_bytes_per_node": FLOW_BYTES[k], "gbs": gbs, "frac_hbm": gbs / hbm}
+        res[cname] = out
     return res
 
 

@@ -268,12 +268,17 @@ typedef struct {
   double detect_hi;  /* detector override C > 0.95 */
   double detect_lo;  /* detector override C < 0.05 */
   int32_t p;         /* polynomial order (1: linear filters) */
+  int32_t compute;   /* NN4_F64 (default): FP64 arithmetic.  NN4_F32: FP32 arithmetic on the FP64
+                        state (C, u, v, w, s_C, C_next stay FP64 in memory; the detector override
+                        is decided on the FP64 C; C_next = C - dt m^-1 s_C adds the FP32 increment
+                        in FP64).  Not in the paper: a precision form of this library. */
 } nn4_vof_params;
 
 /* Fills p with the paper's constants and the given time step. */
 void nn4_vof_params_default(nn4_vof_params* p, double dt);
 
-/* Bytes of device workspace nn4_vof_advect_residual needs for grid g (7 FP64 fields), or -1. */
+/* Bytes of device workspace nn4_vof_advect_residual needs for grid g (the three directional
+ * diffusion coefficient fields k^x, k^y, k^z, sized as FP64), or -1. */
 int64_t nn4_vof_workspace_bytes(const nn4_grid* g);
 
 /* One explicit volume-fraction step (Stage 4 of Section 2.4): s_C of Eq. Petrov-Cs (advection
@@ -282,7 +287,9 @@ int64_t nn4_vof_workspace_bytes(const nn4_grid* g);
  * (Eq. transport-indicator-1, m the lumped nodal volume).  C, u, v, w (q^{n+1}), s_C, C_next:
  * FP64 device arrays on g; workspace: nn4_vof_workspace_bytes(g) bytes of device memory owned by
  * the caller (contents overwritten).  Natural faces for C; the oscillation detector uses the
- * copy-halo of Section 2.3.3 at walls.  All arithmetic FP64. */
+ * copy-halo of Section 2.3.3 at walls.  Arithmetic in p->compute (FP64 by default).
+ * Two launches: the coefficients k^d (Eqs. a_psi to alpha_min_and_max) into the workspace, then
+ * s_C and C_next.  Errors: NN4_EINVAL for a bad grid, parameter or pointer, or outputs aliasing C. */
 int nn4_vof_advect_residual(const nn4_grid* g, const nn4_vof_params* p, const double* C, const double* u,
                             const double* v, const double* w, double* s_C, double* C_next, void* workspace,
                             void* stream);
@@ -291,9 +298,9 @@ int nn4_vof_advect_residual(const nn4_grid* g, const nn4_vof_params* p, const do
  * out all device memory from their own pool or fixed budget, and loops in which the implicit
  * device synchronisation of cudaMalloc / cudaFree is not acceptable.  The paper has no
  * counterpart; this is a deployment variant of nn4_vof_advect_residual.
- * It takes no workspace: its 7-field scratch is a fixed device array inside the library
- * (44 MiB, held by every GPU that loads the library until the process exits) and it calls no
- * allocating routine.  Grids need pitch * ny * nz <= 786432 (e.g. 129 x 65 x 65 with the FP64
+ * It takes no workspace: its scratch (the three coefficient fields) is a fixed device array
+ * inside the library (18 MiB, held by every GPU that loads the library until the process exits)
+ * and it calls no allocating routine.  Grids need pitch * ny * nz <= 786432 (e.g. 129 x 65 x 65 with the FP64
  * pitch); larger grids return NN4_EINVAL with the limit in nn4_last_error().
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.  Every call, on every
@@ -322,6 +329,10 @@ typedef struct {
   int32_t correction_iters;  /* Stage 3 pressure-velocity corrections N_I (2) */
   int32_t pressure_cycles;   /* outer iterations per pressure solve when pressure_rtol <= 0 (20) */
   double pressure_rtol;      /* > 0: solve each pressure equation to this relative residual */
+  int32_t compute;           /* NN4_F64 (default) or NN4_F32: the arithmetic of the explicit terms
+                                (sources, right-hand sides, velocity correction, predictor and the
+                                volume-fraction step); state stays FP64 in memory.  Not in the
+                                paper: a precision form of this library. */
 } nn4_flow_params;
 
 void nn4_flow_params_default(nn4_flow_params* p, double dt);
@@ -329,7 +340,8 @@ void nn4_flow_params_default(nn4_flow_params* p, double dt);
 /* Momentum sources (Eqs. surface-tension-uvw, surface-tension-k, gravity): s_d = sigma_t kappa
  * C_d, and s_z -= g rho, with C_d the pointwise gradient m^-1 f(C; w_d), normals C_d / (eps_t +
  * |grad C|), eps_t = 1e-7 / min(h), kappa = m^-1 sum_d f(n_d; w_d).  s0, s1, s2: outputs; kappa:
- * optional output; workspace: 3 FP64 fields (3 * pitch * ny * nz doubles).  FP64 device arrays on g. */
+ * optional output; workspace: unused (may be NULL; the normals are formed in shared memory).  FP64
+ * device arrays on g; arithmetic in fp->compute. */
 int nn4_momentum_sources(const nn4_grid* g, const nn4_flow_params* fp, const double* C, double* s0, double* s1,
                          double* s2, double* kappa, double* workspace, void* stream);
 
@@ -337,9 +349,13 @@ int nn4_momentum_sources(const nn4_grid* g, const nn4_flow_params* fp, const dou
  * first-derivative filter w_d, 0 on the Dirichlet faces of g (the pressure faces). */
 int nn4_pressure_rhs_hs(const nn4_grid* g, const double* s0, const double* s1, const double* s2, double* b,
                         void* stream);
+/* The same with the arithmetic in `compute` (NN4_F64 or NN4_F32; arrays stay FP64). */
+int nn4_pressure_rhs_hs_ex(const nn4_grid* g, int compute, const double* s0, const double* s1, const double* s2,
+                           double* b, void* stream);
 
 /* Stage-3 right-hand side (Eq. ph_disc2): b = -(1/dt) sum_d [ f(rho u~_d; w_d) - u~_d f(rho; w_d) ],
- * rho from C; 0 on the Dirichlet faces of g.  rho_ws: one FP64 field of workspace. */
+ * rho from C (formed in shared memory); 0 on the Dirichlet faces of g.  rho_ws: unused (may be
+ * NULL).  Arithmetic in fp->compute. */
 int nn4_pressure_rhs_nh(const nn4_grid* g, const nn4_flow_params* fp, const double* C, const double* u,
                         const double* v, const double* w, double* b, double* rho_ws, void* stream);
 
@@ -349,13 +365,16 @@ int nn4_velocity_correct(const nn4_grid* g, const nn4_flow_params* fp, const dou
                          double* v, double* w, double* p_nh, void* stream);
 
 /* One Stage-2 predictor iteration for the three components (Eqs. Petrov-u/v/w, k_Psi-n, k-abs,
- * k-square, max-k, velocity-1 with sigma = 0): from u^n (un), the current u^{n+1/2} (uh, updated in
- * place to (u^n + u~)/2), the total pressure p = p_hs + p_nh and the sources s (from
- * nn4_momentum_sources), writes u~ (ut).  un, uh, ut, s: arrays of three device pointers.
- * Dirichlet faces of g are no-slip walls.  workspace: 5 FP64 fields. */
+ * k-square, max-k, velocity-1 with sigma = 0): from u^n (un), the current u^{n+1/2} (uh), the total
+ * pressure p = p_hs + p_nh and the sources s (from nn4_momentum_sources), writes u~ (ut) and, if
+ * uh_next != NULL, the next u^{n+1/2} = (u^n + u~)/2 (uh_next).  un, uh, ut, uh_next, s: arrays of
+ * three device pointers; ut and uh_next must not alias any input (the filters read uh around each
+ * node).  Dirichlet faces of g are no-slip walls.  workspace: nn4_momentum_workspace_bytes(g)
+ * bytes (the three coefficient fields k_Psi).  Arithmetic in fp->compute. */
+int64_t nn4_momentum_workspace_bytes(const nn4_grid* g);
 int nn4_momentum_predict(const nn4_grid* g, const nn4_flow_params* fp, const double* C, const double* const* un,
-                         double* const* uh, double* const* ut, const double* p, const double* const* s,
-                         double* workspace, void* stream);
+                         const double* const* uh, double* const* ut, double* const* uh_next, const double* p,
+                         const double* const* s, void* workspace, void* stream);
 
 /* A multiphase time stepper: Stage 1 (hydrostatic + surface-tension pressure), Stage 2 (momentum
  * predictor), Stage 3 (N_I non-hydrostatic pressure corrections), Stage 4 (volume fraction) of

@@ -20,7 +20,7 @@ struct FlowImpl {
   size_t f = 0;  // elements per field (pitch * ny * nz)
   double* ws = nullptr;
   // views into ws
-  double *src[3], *stws, *uh[3], *ut[3], *un[3], *ptot, *b, *dp, *mom_ws, *vof_ws, *Cn, *sC, *rho;
+  double *src[3], *uh[3], *uh2[3], *ut[3], *un[3], *ptot, *b, *dp, *mom_ws, *vof_ws, *Cn, *sC;
   double* mass = nullptr;
   unsigned long long* range = nullptr;
 };
@@ -73,7 +73,7 @@ int nn4_flow_create(const nn4_grid* vg, const nn4_grid* pg, const nn4_flow_param
     return rc;
   }
   F->f = (size_t)vg->pitch * vg->n[1] * vg->n[2];
-  const int nfields = 3 + 3 + 3 + 3 + 3 + 1 + 1 + 1 + 5 + 7 + 1 + 1 + 1;
+  const int nfields = 3 + 3 + 3 + 3 + 3 + 1 + 1 + 1 + 3 + 3 + 1 + 1;
   cudaError_t e = cudaMalloc(&F->ws, sizeof(double) * F->f * nfields);
   if (e != cudaSuccess) {
     nn4_plan_destroy(F->plan);
@@ -88,18 +88,17 @@ int nn4_flow_create(const nn4_grid* vg, const nn4_grid* pg, const nn4_flow_param
     return q;
   };
   for (int c = 0; c < 3; ++c) F->src[c] = take(1);
-  F->stws = take(3);
   for (int c = 0; c < 3; ++c) F->uh[c] = take(1);
+  for (int c = 0; c < 3; ++c) F->uh2[c] = take(1);
   for (int c = 0; c < 3; ++c) F->ut[c] = take(1);
   for (int c = 0; c < 3; ++c) F->un[c] = take(1);
   F->ptot = take(1);
   F->b = take(1);
   F->dp = take(1);
-  F->mom_ws = take(5);
-  F->vof_ws = take(7);
+  F->mom_ws = take(3);
+  F->vof_ws = take(3);
   F->Cn = take(1);
   F->sC = take(1);
-  F->rho = take(1);
   if ((rc = check_cuda(cudaMalloc(&F->mass, sizeof(double)), "flow scalars")) ||
       (rc = check_cuda(cudaMalloc(&F->range, 2 * sizeof(unsigned long long)), "flow scalars"))) {
     cudaFree(F->ws);
@@ -138,8 +137,8 @@ int nn4_flow_step(nn4_flow f, double* C, double* u, double* v, double* w, double
   int rc;
   nn4_solve_info info{};
   // Stage 1: sources at level n and the hydrostatic + surface-tension pressure
-  if ((rc = nn4_momentum_sources(&F->vg, &fp, C, F->src[0], F->src[1], F->src[2], nullptr, F->stws, s)) ||
-      (rc = nn4_pressure_rhs_hs(&F->pg, F->src[0], F->src[1], F->src[2], F->b, s)))
+  if ((rc = nn4_momentum_sources(&F->vg, &fp, C, F->src[0], F->src[1], F->src[2], nullptr, nullptr, s)) ||
+      (rc = nn4_pressure_rhs_hs_ex(&F->pg, fp.compute, F->src[0], F->src[1], F->src[2], F->b, s)))
     return rc;
   rc = nn4_pressure_solve(F->plan, F->b, p_hs, rtol, iters, &info, s);
   if (rc && rc != NN4_ENOCONV) return rc;
@@ -147,23 +146,27 @@ int nn4_flow_step(nn4_flow f, double* C, double* u, double* v, double* w, double
     stats->hs_iters = info.iterations;
     stats->hs_rel = info.rel_res;
   }
-  // Stage 2: predictor iterations from u^{n+1/2} = u^n
+  // Stage 2: predictor iterations from u^{n+1/2} = u^n (the iterations alternate between two
+  // u^{n+1/2} buffers: the filters read the current one around every node)
   double* vel[3] = {u, v, w};
-  for (int c = 0; c < 3; ++c) {
-    if ((rc = check_cuda(cudaMemcpyAsync(F->un[c], vel[c], fb, cudaMemcpyDeviceToDevice, s), "copy u")) ||
-        (rc = check_cuda(cudaMemcpyAsync(F->uh[c], vel[c], fb, cudaMemcpyDeviceToDevice, s), "copy u")))
-      return rc;
-  }
+  for (int c = 0; c < 3; ++c)
+    if ((rc = check_cuda(cudaMemcpyAsync(F->un[c], vel[c], fb, cudaMemcpyDeviceToDevice, s), "copy u"))) return rc;
   const int blocks = (int)std::min<size_t>((F->f + 255) / 256, 152 * 16);
   k_add<<<blocks, 256, 0, s>>>(p_hs, p_nh, F->ptot, F->f);
   if ((rc = check_cuda(cudaGetLastError(), "p total"))) return rc;
   const double* unc[3] = {F->un[0], F->un[1], F->un[2]};
   const double* srcc[3] = {F->src[0], F->src[1], F->src[2]};
-  for (int it = 0; it < fp.momentum_iters; ++it)
-    if ((rc = nn4_momentum_predict(&F->vg, &fp, C, unc, F->uh, F->ut, F->ptot, srcc, F->mom_ws, s))) return rc;
+  for (int it = 0; it < fp.momentum_iters; ++it) {
+    double* const* cur = it == 0 ? F->un : (it % 2 ? F->uh : F->uh2);
+    double* const* nxt = it % 2 ? F->uh2 : F->uh;
+    const double* cc[3] = {cur[0], cur[1], cur[2]};
+    const bool last = it + 1 == fp.momentum_iters;
+    if ((rc = nn4_momentum_predict(&F->vg, &fp, C, unc, cc, F->ut, last ? nullptr : nxt, F->ptot, srcc, F->mom_ws, s)))
+      return rc;
+  }
   // Stage 3: non-hydrostatic pressure corrections on u~
   for (int it = 0; it < fp.correction_iters; ++it) {
-    if ((rc = nn4_pressure_rhs_nh(&F->pg, &fp, C, F->ut[0], F->ut[1], F->ut[2], F->b, F->rho, s))) return rc;
+    if ((rc = nn4_pressure_rhs_nh(&F->pg, &fp, C, F->ut[0], F->ut[1], F->ut[2], F->b, nullptr, s))) return rc;
     if ((rc = check_cuda(cudaMemsetAsync(F->dp, 0, fb, s), "zero dp"))) return rc;
     rc = nn4_pressure_solve(F->plan, F->b, F->dp, rtol, iters, &info, s);
     if (rc && rc != NN4_ENOCONV) return rc;
@@ -178,6 +181,7 @@ int nn4_flow_step(nn4_flow f, double* C, double* u, double* v, double* w, double
     if ((rc = check_cuda(cudaMemcpyAsync(vel[c], F->ut[c], fb, cudaMemcpyDeviceToDevice, s), "copy u"))) return rc;
   nn4_vof_params vp;
   nn4_vof_params_default(&vp, fp.dt);
+  vp.compute = fp.compute;
   if ((rc = nn4_vof_advect_residual(&F->vg, &vp, C, u, v, w, F->sC, F->Cn, F->vof_ws, s))) return rc;
   if ((rc = check_cuda(cudaMemcpyAsync(C, F->Cn, fb, cudaMemcpyDeviceToDevice, s), "copy C"))) return rc;
   if (stats) {

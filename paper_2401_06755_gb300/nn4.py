@@ -56,14 +56,14 @@ class _SolveInfo(ctypes.Structure):
 class _VOFParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("dt", "alpha_a", "eps_k", "K_plus", "K_minus", "beta", "eps_x",
                                                "K_pos", "alpha_min", "alpha_max", "detect_hi", "detect_lo")] + \
-               [("p", ctypes.c_int32)]
+               [("p", ctypes.c_int32), ("compute", ctypes.c_int32)]
 
 
 class _FlowParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("dt", "rho_l", "rho_g", "mu_l", "mu_g", "sigma_t", "g", "alpha_a",
                                                "eps_k")] + \
                [("p", ctypes.c_int32), ("momentum_iters", ctypes.c_int32), ("correction_iters", ctypes.c_int32),
-                ("pressure_cycles", ctypes.c_int32), ("pressure_rtol", ctypes.c_double)]
+                ("pressure_cycles", ctypes.c_int32), ("pressure_rtol", ctypes.c_double), ("compute", ctypes.c_int32)]
 
 
 class _FlowStats(ctypes.Structure):
@@ -123,11 +123,13 @@ def lib():
             "nn4_flow_params_default": (None, [ctypes.POINTER(_FlowParams), dbl]),
             "nn4_momentum_sources": (ctypes.c_int, [G, ctypes.POINTER(_FlowParams), vp, vp, vp, vp, vp, vp, vp]),
             "nn4_pressure_rhs_hs": (ctypes.c_int, [G, vp, vp, vp, vp, vp]),
+            "nn4_pressure_rhs_hs_ex": (ctypes.c_int, [G, i32, vp, vp, vp, vp, vp]),
+            "nn4_momentum_workspace_bytes": (ctypes.c_int64, [G]),
             "nn4_pressure_rhs_nh": (ctypes.c_int, [G, ctypes.POINTER(_FlowParams), vp, vp, vp, vp, vp, vp, vp]),
             "nn4_velocity_correct": (ctypes.c_int, [G, ctypes.POINTER(_FlowParams), vp, vp, vp, vp, vp, vp, vp]),
             "nn4_momentum_predict": (ctypes.c_int, [G, ctypes.POINTER(_FlowParams), vp, ctypes.POINTER(vp),
-                                                    ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.POINTER(vp),
-                                                    vp, vp]),
+                                                    ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp,
+                                                    ctypes.POINTER(vp), vp, vp]),
             "nn4_flow_create": (ctypes.c_int, [G, G, ctypes.POINTER(_FlowParams), ctypes.POINTER(_PlanOpts),
                                                ctypes.POINTER(vp)]),
             "nn4_flow_destroy": (ctypes.c_int, [vp]),
@@ -259,9 +261,12 @@ def jacobi_smooth(grid, b, x_in, k=None, x_out=None, omega=2.0 / 3.0, stream=Non
     return x_out
 
 
-def vof_params(dt, **over):
+def vof_params(dt, compute=None, **over):
+    """The scheme's constants with time step dt; compute: F64 (default) or F32 arithmetic."""
     p = _VOFParams()
     lib().nn4_vof_params_default(ctypes.byref(p), float(dt))
+    if compute is not None:
+        p.compute = int(compute)
     for k, v in over.items():
         setattr(p, k, v)
     return p
@@ -272,12 +277,13 @@ def vof_workspace(grid, device="cuda"):
     return torch.empty(int(n) // 8, dtype=torch.float64, device=device)
 
 
-def vof_advect_residual(grid, C, u, v, w, dt, s_C=None, C_next=None, workspace=None, params=None, stream=None):
+def vof_advect_residual(grid, C, u, v, w, dt, s_C=None, C_next=None, workspace=None, params=None, stream=None,
+                        compute=None):
     """One explicit volume-fraction step; returns (s_C, C_next) (FP64 storage tensors)."""
     s_C = torch.empty_like(C) if s_C is None else s_C
     C_next = torch.empty_like(C) if C_next is None else C_next
     workspace = vof_workspace(grid, C.device) if workspace is None else workspace
-    p = vof_params(dt) if params is None else params
+    p = vof_params(dt, compute) if params is None else params
     g = grid.c(torch.float64)
     _check(lib().nn4_vof_advect_residual(ctypes.byref(g), ctypes.byref(p), _ptr(C), _ptr(u), _ptr(v), _ptr(w),
                                          _ptr(s_C), _ptr(C_next), _ptr(workspace), _stream(stream)))
@@ -420,9 +426,13 @@ class Batch:
                        "kernels": infos[i].kernels} for i in range(n)], list(lat)
 
 
-def flow_params(dt, **over):
+def flow_params(dt, compute=None, **over):
+    """Physical constants and scheme settings; compute: F64 (default) or F32 arithmetic of the
+    explicit terms."""
     p = _FlowParams()
     lib().nn4_flow_params_default(ctypes.byref(p), float(dt))
+    if compute is not None:
+        p.compute = int(compute)
     for k, v in over.items():
         setattr(p, k, v)
     return p
@@ -435,26 +445,25 @@ def _arr3(ts):
 def momentum_sources(grid, fp, C, stream=None):
     s = [torch.empty_like(C) for _ in range(3)]
     kappa = torch.empty_like(C)
-    ws = torch.empty((3,) + tuple(C.shape), dtype=torch.float64, device=C.device)
     g = grid.c(torch.float64)
     _check(lib().nn4_momentum_sources(ctypes.byref(g), ctypes.byref(fp), _ptr(C), _ptr(s[0]), _ptr(s[1]),
-                                      _ptr(s[2]), _ptr(kappa), _ptr(ws), _stream(stream)))
+                                      _ptr(s[2]), _ptr(kappa), None, _stream(stream)))
     return s, kappa
 
 
-def pressure_rhs_hs(pgrid, s, stream=None):
+def pressure_rhs_hs(pgrid, s, stream=None, compute=F64):
     b = torch.empty_like(s[0])
     g = pgrid.c(torch.float64)
-    _check(lib().nn4_pressure_rhs_hs(ctypes.byref(g), _ptr(s[0]), _ptr(s[1]), _ptr(s[2]), _ptr(b), _stream(stream)))
+    _check(lib().nn4_pressure_rhs_hs_ex(ctypes.byref(g), int(compute), _ptr(s[0]), _ptr(s[1]), _ptr(s[2]), _ptr(b),
+                                        _stream(stream)))
     return b
 
 
 def pressure_rhs_nh(pgrid, fp, C, ut, stream=None):
     b = torch.empty_like(C)
-    rho = torch.empty_like(C)
     g = pgrid.c(torch.float64)
     _check(lib().nn4_pressure_rhs_nh(ctypes.byref(g), ctypes.byref(fp), _ptr(C), _ptr(ut[0]), _ptr(ut[1]),
-                                     _ptr(ut[2]), _ptr(b), _ptr(rho), _stream(stream)))
+                                     _ptr(ut[2]), _ptr(b), None, _stream(stream)))
     return b
 
 
@@ -465,14 +474,20 @@ def velocity_correct(vgrid, fp, C, dp, u, p_nh=None, stream=None):
     return u
 
 
-def momentum_predict(vgrid, fp, C, un, uh, p, s, stream=None):
-    """One predictor iteration; uh is updated in place; returns u~."""
-    ut = [torch.empty_like(C) for _ in range(3)]
-    ws = torch.empty((5,) + tuple(C.shape), dtype=torch.float64, device=C.device)
+def momentum_workspace(grid, device="cuda"):
+    n = lib().nn4_momentum_workspace_bytes(ctypes.byref(grid.c(torch.float64)))
+    return torch.empty(int(n) // 8, dtype=torch.float64, device=device)
+
+
+def momentum_predict(vgrid, fp, C, un, uh, p, s, ut=None, uh_next=None, workspace=None, stream=None):
+    """One predictor iteration from u^n (un) and u^{n+1/2} (uh); returns (u~, the next u^{n+1/2})."""
+    ut = [torch.empty_like(C) for _ in range(3)] if ut is None else ut
+    uh_next = [torch.empty_like(C) for _ in range(3)] if uh_next is None else uh_next
+    ws = momentum_workspace(vgrid, C.device) if workspace is None else workspace
     g = vgrid.c(torch.float64)
     _check(lib().nn4_momentum_predict(ctypes.byref(g), ctypes.byref(fp), _ptr(C), _arr3(un), _arr3(uh), _arr3(ut),
-                                      _ptr(p), _arr3(s), _ptr(ws), _stream(stream)))
-    return ut
+                                      _arr3(uh_next), _ptr(p), _arr3(s), _ptr(ws), _stream(stream)))
+    return ut, uh_next
 
 
 class Flow:

@@ -37,3 +37,15 @@ def abs_bound(g, x, k=None):
     ak, ax = np.abs(k), np.abs(x)
     return 0.5 * (fem.apply_assembled(Ae, ak * ax) + ak * fem.apply_assembled(Ae, ax)
                   + ax * fem.apply_assembled(Ae, ak))
+
+
+def check_close(name, got, ref, rel, scale=None):
+    """Max-norm error relative to the reference field's scale (or `scale`), at most `rel`.
+
+    Prints the measured ratio (``PARITY name value``) so that the tolerances can be set from
+    the errors actually reached; returns it."""
+    scale = max(float(np.abs(ref).max()) if scale is None else float(scale), 1e-300)
+    err = float(np.abs(np.asarray(got) - np.asarray(ref)).max()) / scale
+    print(f"PARITY {name} {err:.3e} (tol {rel:.1e})")
+    assert err <= rel, f"{name}: max rel err {err:.3e} > {rel:.1e}"
+    return err

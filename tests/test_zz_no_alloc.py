@@ -4,8 +4,8 @@ For callers that cannot allocate device memory (a host that owns all device memo
 own pool, or a loop that must not take the device synchronisation of cudaMalloc / cudaFree):
 nn4_vof_advect_residual_static keeps its scratch in a fixed device array inside the library.
 This test compares it with nn4_vof_advect_residual (caller-provided workspace) on two calls in
-a row with different inputs, within the tolerance of the other flow tests.  It lives in a file
-that pytest collects last.
+a row with different inputs, larger grid first, bit for bit.  It lives in a file that pytest
+collects last.
 """
 
 import ctypes
@@ -21,7 +21,7 @@ from tests.test_gpu_flow import _velocity
 pytestmark = pytest.mark.gpu
 
 
-def _call_static(nn4, G, C, u, v, w, dt):
+def _call_static(nn4, G, C, u, v, w, dt, compute):
     L = nn4.lib()
     fn = L.nn4_vof_advect_residual_static
     fn.restype = ctypes.c_int
@@ -30,33 +30,36 @@ def _call_static(nn4, G, C, u, v, w, dt):
     s = torch.empty_like(C)
     Cn = torch.empty_like(C)
     g = G.c(torch.float64)
-    p = nn4.vof_params(dt)
+    p = nn4.vof_params(dt, compute)
     rc = fn(ctypes.byref(g), ctypes.byref(p), nn4._ptr(C), nn4._ptr(u), nn4._ptr(v), nn4._ptr(w), nn4._ptr(s),
             nn4._ptr(Cn), nn4._stream(None))
     assert rc == nn4.OK, L.nn4_last_error()
     return s, Cn
 
 
-def test_static_scratch_matches_workspace_version_twice():
+@pytest.mark.parametrize("compute", ["f64", "f32"])
+def test_static_scratch_matches_workspace_version_twice(compute):
+    """Two calls in a row, the larger grid first: a scratch element the second call failed to
+    write would still hold the first call's value.  Both entry points run the same kernels on
+    the same inputs, so their results are compared bit for bit."""
     need_gpu()
     from paper_2401_06755_gb300 import nn4
+    cm = nn4.F64 if compute == "f64" else nn4.F32
     cases = [
-        ((33, 17, 17), (1 / 32, 1 / 64, 1 / 32), "column", 1e-4, 4),
         ((37, 29, 41), (1 / 36,) * 3, "bubble", 2e-4, 5),
+        ((33, 17, 17), (1 / 32, 1 / 64, 1 / 32), "column", 1e-4, 4),
     ]
-    for n, h, kind, dt, seed in cases:  # two calls in a row, different grids and inputs
+    for n, h, kind, dt, seed in cases:
         C = column_field(n, h, 0.25, 0.25) if kind == "column" else sphere_ramp_field(n, h, (0.5, 0.4, 0.45), 0.25, 2 * h[0])
         u, v, w = _velocity(n, h, seed)
         G = nn4.Grid(n, h)
         dev = lambda a: nn4.to_field(a, G)
         Cd, ud, vd, wd = dev(C), dev(u), dev(v), dev(w)
-        s_ref, Cn_ref = nn4.vof_advect_residual(G, Cd, ud, vd, wd, dt)
-        s, Cn = _call_static(nn4, G, Cd, ud, vd, wd, dt)
+        s_ref, Cn_ref = nn4.vof_advect_residual(G, Cd, ud, vd, wd, dt, compute=cm)
+        s, Cn = _call_static(nn4, G, Cd, ud, vd, wd, dt, cm)
         torch.cuda.synchronize()
-        a, b = nn4.nodes(s, G).cpu().numpy(), nn4.nodes(s_ref, G).cpu().numpy()
-        assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
-        a, b = nn4.nodes(Cn, G).cpu().numpy(), nn4.nodes(Cn_ref, G).cpu().numpy()
-        assert np.abs(a - b).max() <= 1e-10
+        assert torch.equal(nn4.nodes(s, G), nn4.nodes(s_ref, G)), kind
+        assert torch.equal(nn4.nodes(Cn, G), nn4.nodes(Cn_ref, G)), kind
 
 
 def test_static_scratch_rejects_large_grids():
