@@ -493,10 +493,12 @@ def momentum_predict(vgrid, fp, C, un, uh, p, s, ut=None, uh_next=None, workspac
 class Flow:
     """The four-stage multiphase time step on device state (Section 2.4)."""
 
-    def __init__(self, vgrid, pgrid, fp, inner=F64, inner_cycles=1, outer=OUTER_CYCLES):
+    def __init__(self, vgrid, pgrid, fp, inner=F64, inner_cycles=1, outer=OUTER_CYCLES, inner_krylov=0,
+                 check_every=1):
         o = _PlanOpts()
         lib().nn4_plan_opts_default(ctypes.byref(o))
         o.inner, o.inner_cycles, o.outer = int(inner), int(inner_cycles), int(outer)
+        o.inner_krylov, o.check_every = int(inner_krylov), int(check_every)
         self._gv, self._gp = vgrid.c(torch.float64), pgrid.c(torch.float64)
         self.fp = fp
         h = ctypes.c_void_p(0)

@@ -19,8 +19,13 @@ def test_roofline_entry_flops_and_bytes():
     r = bench.roofline_entry(("pass27:jacobi:L1", (2, 0.128)), n, 1.2, 6674.5, s=4)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(120.0 * 129 ** 3 / 64e-6 / 1e9)
-    # storage-dependent bytes: BF16 halves the stored values of the level-0 sweep
-    assert bench.bytes_per_node("pass:jacobi:L0", 2) == 16 and bench.bytes_per_node("pass:jacobi:L0", 4) == 28
+    # the method's bytes (x, k, b in, e out, the FP32 q of the fused dot); BF16 halves the stored
+    # values; the precomputed (1/2) L k and 1/diag are reported apart
+    assert bench.bytes_per_node("pass:jacobi:L0", 2) == 12 and bench.bytes_per_node("pass:jacobi:L0", 4) == 20
+    assert bench.aux_bytes_per_node("pass:jacobi:L0", 4) == 8
+    r = bench.roofline_entry(("pass:jacobi:L0", (1, 0.1)), n, 1.2, 6674.5, s=4)
+    assert r["frac"] == pytest.approx(20 * n ** 3 / 1e-4 / 1e9 / 6674.5)
+    assert r["frac_with_aux"] == pytest.approx(28 * n ** 3 / 1e-4 / 1e9 / 6674.5)
     assert bench.bytes_per_node("restrict:L0", 4) == 4.5
     assert bench.roofline_entry(("unknown", (1, 1.0)), n, 1.2, 6674.5)["bound"] is None
 
