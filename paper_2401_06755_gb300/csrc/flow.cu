@@ -81,17 +81,39 @@ struct VofK {
   double detect_hi, detect_lo;
 };
 
-template <typename T, int RY, int TYT>
-__global__ void __launch_bounds__(32 * TYT) k_vof_coef(const Geo<T> g, const VofK<T> p, int zc,
-                                                       const double* __restrict__ C, const double* __restrict__ u,
-                                                       const double* __restrict__ v, const double* __restrict__ w,
-                                                       T* __restrict__ kx, T* __restrict__ ky, T* __restrict__ kz) {
+template <typename T, int RY, int TYT, int NS>
+__global__ void __launch_bounds__(32 * TYT) k_vof_coef(const __grid_constant__ ft::FMaps maps, const Geo<T> g,
+                                                       const VofK<T> p, int zc, const double* __restrict__ C,
+                                                       const double* __restrict__ u, const double* __restrict__ v,
+                                                       const double* __restrict__ w, T* __restrict__ kx,
+                                                       T* __restrict__ ky, T* __restrict__ kz) {
   constexpr int NT = 32 * TYT, TY = TYT * RY, SW = 34, SH = TY + 2;
-  __shared__ T sC[2][SH * SW];
-  __shared__ T sg[SH * SW];
+  using BC = ft::Halo2<SH>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* const cs = reinterpret_cast<T*>(smem + NS * BC::BYTES);  // compute slots [2][SH * SW]
+  T* const sg = cs + 2 * SH * SW;                             // g of plane t, tile plus halo
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
   const int X0 = blockIdx.x * 30, Y0 = blockIdx.y * (TY - 2);
   const int gx = X0 - 1 + tx, R0 = ty * RY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
+  ft::Ring<NS> ring{reinterpret_cast<uint64_t*>(sg + SH * SW), smem, BC::BYTES, z0 - 2};
+  const int last = z1 + 1;
+  auto issue = [&](int z) {
+    mbar_expect_tx(ring.barrier(z), BC::TX);
+    tma_load_3d(ring.at(z), &maps.m[0], X0 - 2, Y0 - 2, z, ring.barrier(z));
+  };
+  if (tid == 0) ring.init();
+  for (int i = tid; i < SH * SW; i += NT) sg[i] = T(0);
+  __syncthreads();
+  if (tid == 0)
+    for (int z = ring.j0; z <= min(last, ring.j0 + NS - 2); ++z) issue(z);
+  bool failed = !ring.wait(ring.j0);
+  ft::convert_box<BC, SW, SH, NT>(cs, ring.at(ring.j0), tid);
+  if (__syncthreads_or(failed)) {
+    if (tid == 0) ring.drain(ring.j0, min(last, ring.j0 + NS - 2));
+    return;
+  }
+
   const Fac<T> FX = ft::facx(g, gx);
   W3<T> yM[RY], yG[RY];
   T ly[RY];
@@ -107,52 +129,43 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_coef(const Geo<T> g, const Vof
     in[r] = gx >= 0 && gx < g.nx && gy[r] >= 0 && gy[r] < g.ny;
     outp[r] = in[r] && tx >= 1 && tx <= 30 && R0 + r >= 1 && R0 + r <= TY - 2;
   }
-  for (int i = tid; i < SH * SW; i += NT) sg[i] = T(0);
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
-  ft::Stage<double, SW, SH, NT> st;
-  st.issue(C, g, X0 - 2, Y0 - 2, z0 - 2, tid);
-  st.commit(sC[0], tid);
-  __syncthreads();
-
+  const bool wx0 = gx == 0, wx1 = gx == g.nx - 1;
   T gacc[3][RY][3], aacc[RY][3];
   T Cdq[3][RY], gq[RY], Uq[3][RY], Szq[RY];      // plane q = s - 2 (saved at step s - 1)
   T SxR[2][RY], SyR[2][RY], CnR[2][RY];          // detectors and node value of planes s - 2, s - 1
+  double Ur[3][RY], cr[RY];                      // prefetched: u, v, w of plane s - 1; C of plane s - 2
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       gacc[0][r][c] = gacc[1][r][c] = gacc[2][r][c] = aacc[r][c] = T(0);
       Cdq[c][r] = Uq[c][r] = T(0);
+      Ur[c][r] = 0.0;
     }
     gq[r] = Szq[r] = T(0);
+    cr[r] = 0.0;
     SxR[0][r] = SxR[1][r] = SyR[0][r] = SyR[1][r] = CnR[0][r] = CnR[1][r] = T(0);
   }
 
-  for (int s = z0 - 2; s <= z1 + 1; ++s) {
-    const int sl = (s - z0) & 1;
-    if (s <= z1) st.issue(C, g, X0 - 2, Y0 - 2, s + 1, tid);
+  for (int s = ring.j0; s <= last; ++s) {
+    if (tid == 0 && s + NS - 1 <= last) issue(s + NS - 1);
+    const T* cur = cs + ((s - ring.j0) & 1) * SH * SW;
     const int t = s - 1, q = s - 2;
     const bool tin = t >= 0 && t < g.nz;
     const bool emit = q >= z0 && q < z1;
     T Ut[3][RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Ut[d][r] = ft::from64<T>(Ur[d][r]);
     double c64[RY];
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-      if (tin && in[r]) {
-        const long long o = (long long)t * g.plane + (long long)gy[r] * g.pitch + gx;
-        Ut[0][r] = ft::load_as<T>(u + o);
-        Ut[1][r] = ft::load_as<T>(v + o);
-        Ut[2][r] = ft::load_as<T>(w + o);
-      } else {
-        Ut[0][r] = Ut[1][r] = Ut[2][r] = T(0);
-      }
-      c64[r] = (emit && outp[r]) ? __ldg(C + (long long)q * g.plane + (long long)gy[r] * g.pitch + gx) : 0.0;
-    }
+    for (int r = 0; r < RY; ++r) c64[r] = cr[r];
     // plane s: x-y filters of C, detectors along x and y, node value
     T SxN[RY], SyN[RY], CnN[RY];
     if (s >= 0 && s < g.nz) {
       T vv[RY + 2][3];
-      ft::nb<T, RY, SW>(sC[sl], R0, tx, vv);
+      ft::nb<T, RY, SW>(cur, R0, tx, vv);
       T xG[RY + 2], xM[RY + 2], GM[RY], MG[RY], MM[RY];
       ft::xpass<T, RY>(vv, FX.G, xG);
       ft::xpass<T, RY>(vv, FX.M, xM);
@@ -166,10 +179,11 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_coef(const Geo<T> g, const Vof
         ft::zacc(gacc[1][r], MG[r], zp.M, zs.M, zn.M);
         ft::zacc(gacc[2][r], MM[r], zp.G, zs.G, zn.G);
         const T c0 = vv[r + 1][1];
-        // the copy-halo of the detector at walls: the staged neighbour index is clamped onto
-        // the wall node itself
-        SxN[r] = (c0 - vv[r + 1][0]) * (vv[r + 1][2] - c0);
-        SyN[r] = (c0 - vv[r][1]) * (vv[r + 2][1] - c0);
+        // the copy-halo of the detector at walls: the missing neighbour takes the wall value
+        const T xl = wx0 ? c0 : vv[r + 1][0], xr = wx1 ? c0 : vv[r + 1][2];
+        const T yl = gy[r] == 0 ? c0 : vv[r][1], yr = gy[r] == g.ny - 1 ? c0 : vv[r + 2][1];
+        SxN[r] = (c0 - xl) * (xr - c0);
+        SyN[r] = (c0 - yl) * (yr - c0);
         CnN[r] = c0;
       }
     } else {
@@ -198,6 +212,16 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_coef(const Geo<T> g, const Vof
 #pragma unroll
         for (int d = 0; d < 3; ++d) ft::zshift(gacc[d][r]);
       }
+    }
+    // prefetch for the next step: u, v, w of plane s and C of plane s - 1
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      const bool ok = in[r] && s >= 0 && s < g.nz;
+      const long long o = (long long)s * g.plane + (long long)gy[r] * g.pitch + gx;
+      Ur[0][r] = ok ? __ldg(u + o) : 0.0;
+      Ur[1][r] = ok ? __ldg(v + o) : 0.0;
+      Ur[2][r] = ok ? __ldg(w + o) : 0.0;
+      cr[r] = (outp[r] && t >= z0 && t < z1) ? __ldg(C + o - g.plane) : 0.0;
     }
     __syncthreads();
     // mass filter of g at plane t: completes M g at plane q
@@ -262,27 +286,69 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_coef(const Geo<T> g, const Vof
       CnR[0][r] = CnR[1][r];
       CnR[1][r] = CnN[r];
     }
-    st.commit(sC[sl ^ 1], tid);
-    __syncthreads();
+    if (s < last) {
+      if (!ring.wait(s + 1)) failed = true;
+      ft::convert_box<BC, SW, SH, NT>(cs + ((s + 1 - ring.j0) & 1) * SH * SW, ring.at(s + 1), tid);
+    }
+    if (__syncthreads_or(failed)) {
+      if (tid == 0) ring.drain(s + 1, min(last, s + NS - 1));
+      return;
+    }
   }
+}
+
+template <typename T, int TY, int NS>
+constexpr int vof_coef_smem() {
+  return NS * ft::Halo2<TY + 2>::BYTES + 3 * (TY + 2) * 34 * (int)sizeof(T) + NS * 8;
 }
 
 // ---------------------------------------------------------------- volume fraction, stage B
 // s_C = sum_d u_d f(C; w_d) + sum_d (1/2)[D_d(k^d C) + k^d D_d C - C D_d k^d] (Eq. Petrov-Cs with
 // the directional filters D_x = K (x) M (x) M, ... in the form of Eq. k-Txx) and C_next = C - dt
 // s_C / m (Eq. transport-indicator-1).
-template <typename T, int RY, int TYT>
-__global__ void __launch_bounds__(32 * TYT) k_vof_update(const Geo<T> g, double dt, T dtT, int zc,
-                                                         const double* __restrict__ C, const T* __restrict__ kx,
-                                                         const T* __restrict__ ky, const T* __restrict__ kz,
+template <typename T, int RY, int TYT, int NS>
+__global__ void __launch_bounds__(32 * TYT) k_vof_update(const __grid_constant__ ft::FMaps maps, const Geo<T> g,
+                                                         double dt, T dtT, int zc, const double* __restrict__ C,
                                                          const double* __restrict__ u, const double* __restrict__ v,
                                                          const double* __restrict__ w, double* __restrict__ sC,
                                                          double* __restrict__ Cnext) {
   constexpr int NT = 32 * TYT, TY = TYT * RY, SW = 34, SH = TY + 2;
-  __shared__ T sh[2][4][SH * SW];
+  using BC = ft::Halo1<double, SH>;
+  using BK = ft::Halo1<T, SH>;
+  constexpr int SLOT = BC::BYTES + 3 * BK::BYTES;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* const cs = reinterpret_cast<T*>(smem + NS * SLOT);  // compute slots [2][4][SH * SW]: C, k^x, k^y, k^z
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
   const int X0 = blockIdx.x * 32, Y0 = blockIdx.y * TY;
   const int gx = X0 + tx, R0 = ty * RY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
+  ft::Ring<NS> ring{reinterpret_cast<uint64_t*>(cs + 2 * 4 * SH * SW), smem, SLOT, z0 - 1};
+  const int last = z1;
+  auto issue = [&](int z) {
+    unsigned char* d = ring.at(z);
+    mbar_expect_tx(ring.barrier(z), BC::TX + 3 * BK::TX);
+    tma_load_3d(d, &maps.m[0], X0 - 1 - BC::CO, Y0 - 1, z, ring.barrier(z));
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+      tma_load_3d(d + BC::BYTES + f * BK::BYTES, &maps.m[1 + f], X0 - 1 - BK::CO, Y0 - 1, z, ring.barrier(z));
+  };
+  auto convert = [&](int z, T* dst) {
+    const unsigned char* src = ring.at(z);
+    ft::convert_box<BC, SW, SH, NT>(dst, src, tid);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) ft::convert_box<BK, SW, SH, NT>(dst + (1 + f) * SH * SW, src + BC::BYTES + f * BK::BYTES, tid);
+  };
+  if (tid == 0) ring.init();
+  __syncthreads();
+  if (tid == 0)
+    for (int z = ring.j0; z <= min(last, ring.j0 + NS - 2); ++z) issue(z);
+  bool failed = !ring.wait(ring.j0);
+  convert(ring.j0, cs);
+  if (__syncthreads_or(failed)) {
+    if (tid == 0) ring.drain(ring.j0, min(last, ring.j0 + NS - 2));
+    return;
+  }
+
   const Fac<T> FX = ft::facx(g, gx);
   W3<T> yM[RY], yG[RY], yK[RY];
   T ly[RY];
@@ -298,58 +364,31 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_update(const Geo<T> g, double 
     ly[r] = fy.lump;
     in[r] = gx < g.nx && gy[r] < g.ny;
   }
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
-  ft::Stage<double, SW, SH, NT> stC;
-  ft::Stage<T, SW, SH, NT> stK[3];
-  const T* kf[3] = {kx, ky, kz};
-  stC.issue(C, g, X0 - 1, Y0 - 1, z0 - 1, tid);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) stK[d].issue(kf[d], g, X0 - 1, Y0 - 1, z0 - 1, tid);
-  stC.commit(sh[0][0], tid);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) stK[d].commit(sh[0][1 + d], tid);
-  __syncthreads();
-
   // accumulators: f_x, f_y, f_z (raw gradient of C), D_x C, D_y C, D_z C, sum_d D_d(k^d C),
   // sum_d D_d k^d
   T A[8][RY][3];
   T Cq[RY], kq[3][RY];
+  double Ur[3][RY], cr[RY];  // prefetched u, v, w and C of plane s - 1
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int r = 0; r < RY; ++r) A[a][r][0] = A[a][r][1] = A[a][r][2] = T(0);
 #pragma unroll
-  for (int r = 0; r < RY; ++r) Cq[r] = kq[0][r] = kq[1][r] = kq[2][r] = T(0);
+  for (int r = 0; r < RY; ++r) {
+    Cq[r] = kq[0][r] = kq[1][r] = kq[2][r] = T(0);
+    Ur[0][r] = Ur[1][r] = Ur[2][r] = cr[r] = 0.0;
+  }
 
-  for (int s = z0 - 1; s <= z1; ++s) {
-    const int sl = (s - z0 + 1) & 1;
-    if (s < z1) {
-      stC.issue(C, g, X0 - 1, Y0 - 1, s + 1, tid);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) stK[d].issue(kf[d], g, X0 - 1, Y0 - 1, s + 1, tid);
-    }
+  for (int s = ring.j0; s <= last; ++s) {
+    if (tid == 0 && s + NS - 1 <= last) issue(s + NS - 1);
+    const T* cur = cs + ((s - ring.j0) & 1) * 4 * SH * SW;
     const int q = s - 1;
     const bool emit = q >= z0;
-    T U[3][RY];
-    double c64[RY];
-#pragma unroll
-    for (int r = 0; r < RY; ++r) {
-      if (emit && in[r]) {
-        const long long o = (long long)q * g.plane + (long long)gy[r] * g.pitch + gx;
-        U[0][r] = ft::load_as<T>(u + o);
-        U[1][r] = ft::load_as<T>(v + o);
-        U[2][r] = ft::load_as<T>(w + o);
-        c64[r] = __ldg(C + o);
-      } else {
-        U[0][r] = U[1][r] = U[2][r] = T(0);
-        c64[r] = 0.0;
-      }
-    }
     T CnN[RY], kN[3][RY];
     if (s >= 0 && s < g.nz) {
       const Fac<T> zp = ft::facz(g, s - 1), zs = ft::facz(g, s), zn = ft::facz(g, s + 1);
       T vC[RY + 2][3];
-      ft::nb<T, RY, SW>(sh[sl][0], R0, tx, vC);
+      ft::nb<T, RY, SW>(cur, R0, tx, vC);
       {
         T xG[RY + 2], xM[RY + 2], xK[RY + 2], P[RY];
         ft::xpass<T, RY>(vC, FX.G, xG);
@@ -380,7 +419,7 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_update(const Geo<T> g, double 
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         T vk[RY + 2][3], vkc[RY + 2][3];
-        ft::nb<T, RY, SW>(sh[sl][1 + d], R0, tx, vk);
+        ft::nb<T, RY, SW>(cur + (1 + d) * SH * SW, R0, tx, vk);
 #pragma unroll
         for (int rr = 0; rr < RY + 2; ++rr)
 #pragma unroll
@@ -416,7 +455,8 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_update(const Geo<T> g, double 
 #pragma unroll
       for (int r = 0; r < RY; ++r) {
         if (!in[r]) continue;
-        const T sv = U[0][r] * A[0][r][0] + U[1][r] * A[1][r][0] + U[2][r] * A[2][r][0] +
+        const T sv = ft::from64<T>(Ur[0][r]) * A[0][r][0] + ft::from64<T>(Ur[1][r]) * A[1][r][0] +
+                     ft::from64<T>(Ur[2][r]) * A[2][r][0] +
                      T(0.5) * (A[6][r][0] + kq[0][r] * A[3][r][0] + kq[1][r] * A[4][r][0] + kq[2][r] * A[5][r][0] -
                                Cq[r] * A[7][r][0]);
         const long long o = (long long)q * g.plane + (long long)gy[r] * g.pitch + gx;
@@ -424,12 +464,22 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_update(const Geo<T> g, double 
         if (Cnext) {
           const T m = FX.lump * ly[r] * lz;
           if constexpr (sizeof(T) == 8) {
-            Cnext[o] = c64[r] - dt * (double)sv / (double)m;
+            Cnext[o] = cr[r] - dt * (double)sv / (double)m;
           } else {
-            Cnext[o] = c64[r] - ft::to64(dtT * sv / m);
+            Cnext[o] = cr[r] - ft::to64(dtT * sv / m);
           }
         }
       }
+    }
+    // prefetch for the next step: u, v, w, C of plane s (emitted then)
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      const bool ok = in[r] && s >= z0 && s < z1;
+      const long long o = (long long)s * g.plane + (long long)gy[r] * g.pitch + gx;
+      Ur[0][r] = ok ? __ldg(u + o) : 0.0;
+      Ur[1][r] = ok ? __ldg(v + o) : 0.0;
+      Ur[2][r] = ok ? __ldg(w + o) : 0.0;
+      cr[r] = ok ? __ldg(C + o) : 0.0;
     }
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
@@ -439,11 +489,21 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_update(const Geo<T> g, double 
 #pragma unroll
       for (int d = 0; d < 3; ++d) kq[d][r] = kN[d][r];
     }
-    stC.commit(sh[sl ^ 1][0], tid);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) stK[d].commit(sh[sl ^ 1][1 + d], tid);
-    __syncthreads();
+    if (s < last) {
+      if (!ring.wait(s + 1)) failed = true;
+      convert(s + 1, cs + ((s + 1 - ring.j0) & 1) * 4 * SH * SW);
+    }
+    if (__syncthreads_or(failed)) {
+      if (tid == 0) ring.drain(s + 1, min(last, s + NS - 1));
+      return;
+    }
   }
+}
+
+template <typename T, int TY, int NS>
+constexpr int vof_update_smem() {
+  return NS * (ft::Halo1<double, TY + 2>::BYTES + 3 * ft::Halo1<T, TY + 2>::BYTES) +
+         2 * 4 * (TY + 2) * 34 * (int)sizeof(T) + NS * 8;
 }
 
 // ---------------------------------------------------------------- momentum sources
@@ -455,17 +515,37 @@ struct SrcK {
   T eps_t, sigma, grho_g, grho_d;  // g rho = grho_g + grho_d C
 };
 
-template <typename T, int RY, int TYT>
-__global__ void __launch_bounds__(32 * TYT) k_sources(const Geo<T> g, const SrcK<T> p, int zc,
-                                                      const double* __restrict__ C, double* __restrict__ s0,
-                                                      double* __restrict__ s1, double* __restrict__ s2,
-                                                      double* __restrict__ kappa) {
+template <typename T, int RY, int TYT, int NS>
+__global__ void __launch_bounds__(32 * TYT) k_sources(const __grid_constant__ ft::FMaps maps, const Geo<T> g,
+                                                      const SrcK<T> p, int zc, const double* __restrict__ C,
+                                                      double* __restrict__ s0, double* __restrict__ s1,
+                                                      double* __restrict__ s2, double* __restrict__ kappa) {
   constexpr int NT = 32 * TYT, TY = TYT * RY, SW = 34, SH = TY + 2;
-  __shared__ T sC[2][SH * SW];
-  __shared__ T sn[3][SH * SW];
+  using BC = ft::Halo2<SH>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* const cs = reinterpret_cast<T*>(smem + NS * BC::BYTES);  // compute slots [2][SH * SW]
+  T* const sn = cs + 2 * SH * SW;                             // normals [3][SH * SW] of plane t
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
   const int X0 = blockIdx.x * 30, Y0 = blockIdx.y * (TY - 2);
   const int gx = X0 - 1 + tx, R0 = ty * RY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
+  ft::Ring<NS> ring{reinterpret_cast<uint64_t*>(sn + 3 * SH * SW), smem, BC::BYTES, z0 - 2};
+  const int last = z1 + 1;
+  auto issue = [&](int z) {
+    mbar_expect_tx(ring.barrier(z), BC::TX);
+    tma_load_3d(ring.at(z), &maps.m[0], X0 - 2, Y0 - 2, z, ring.barrier(z));
+  };
+  if (tid == 0) ring.init();
+  for (int i = tid; i < 3 * SH * SW; i += NT) sn[i] = T(0);
+  __syncthreads();
+  if (tid == 0)
+    for (int z = ring.j0; z <= min(last, ring.j0 + NS - 2); ++z) issue(z);
+  bool failed = !ring.wait(ring.j0);
+  ft::convert_box<BC, SW, SH, NT, true>(cs, ring.at(ring.j0), tid);
+  if (__syncthreads_or(failed)) {
+    if (tid == 0) ring.drain(ring.j0, min(last, ring.j0 + NS - 2));
+    return;
+  }
   const Fac<T> FX = ft::facx(g, gx);
   W3<T> yM[RY], yG[RY];
   T ly[RY];
@@ -481,32 +561,27 @@ __global__ void __launch_bounds__(32 * TYT) k_sources(const Geo<T> g, const SrcK
     in[r] = gx >= 0 && gx < g.nx && gy[r] >= 0 && gy[r] < g.ny;
     outp[r] = in[r] && tx >= 1 && tx <= 30 && R0 + r >= 1 && R0 + r <= TY - 2;
   }
-  for (int i = tid; i < 3 * SH * SW; i += NT) (&sn[0][0])[i] = T(0);
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
-  ft::Stage<double, SW, SH, NT> st;
-  st.issue(C, g, X0 - 2, Y0 - 2, z0 - 2, tid);
-  st.commit(sC[0], tid);
-  __syncthreads();
-
   T gacc[3][RY][3], kacc[RY][3], Cdq[3][RY];
+  double cr[RY];  // prefetched C of plane s - 2
 #pragma unroll
-  for (int r = 0; r < RY; ++r)
+  for (int r = 0; r < RY; ++r) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) gacc[0][r][c] = gacc[1][r][c] = gacc[2][r][c] = kacc[r][c] = Cdq[c][r] = T(0);
+    cr[r] = 0.0;
+  }
 
-  for (int s = z0 - 2; s <= z1 + 1; ++s) {
-    const int sl = (s - z0) & 1;
-    if (s <= z1) st.issue(C, g, X0 - 2, Y0 - 2, s + 1, tid);
+  for (int s = ring.j0; s <= last; ++s) {
+    if (tid == 0 && s + NS - 1 <= last) issue(s + NS - 1);
+    const T* cur = cs + ((s - ring.j0) & 1) * SH * SW;
     const int t = s - 1, q = s - 2;
     const bool tin = t >= 0 && t < g.nz;
     const bool emit = q >= z0 && q < z1;
     double c64[RY];
 #pragma unroll
-    for (int r = 0; r < RY; ++r)
-      c64[r] = (emit && outp[r]) ? __ldg(C + (long long)q * g.plane + (long long)gy[r] * g.pitch + gx) : 0.0;
+    for (int r = 0; r < RY; ++r) c64[r] = cr[r];
     if (s >= 0 && s < g.nz) {
       T vv[RY + 2][3], xG[RY + 2], xM[RY + 2], GM[RY], MG[RY], MM[RY];
-      ft::nb<T, RY, SW>(sC[sl], R0, tx, vv);
+      ft::nb<T, RY, SW>(cur, R0, tx, vv);
       ft::xpass<T, RY>(vv, FX.G, xG);
       ft::xpass<T, RY>(vv, FX.M, xM);
       ft::ypass<T, RY>(xG, yM, GM);
@@ -538,24 +613,29 @@ __global__ void __launch_bounds__(32 * TYT) k_sources(const Geo<T> g, const SrcK
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          sn[d][(R0 + r + 1) * SW + tx + 1] = n[d];
+          sn[d * SH * SW + (R0 + r + 1) * SW + tx + 1] = n[d];
           ft::zshift(gacc[d][r]);
         }
       }
     }
+    // prefetch C of plane t (emitted at the next step)
+#pragma unroll
+    for (int r = 0; r < RY; ++r)
+      cr[r] = (outp[r] && t >= z0 && t < z1) ? __ldg(C + (long long)t * g.plane + (long long)gy[r] * g.pitch + gx)
+                                             : 0.0;
     __syncthreads();
     if (tin) {
       const Fac<T> zp = ft::facz(g, t - 1), zs = ft::facz(g, t), zn = ft::facz(g, t + 1);
       T vn[RY + 2][3], xr[RY + 2], P[RY], P2[RY];
-      ft::nb<T, RY, SW>(sn[0], R0, tx, vn);
+      ft::nb<T, RY, SW>(sn, R0, tx, vn);
       ft::xpass<T, RY>(vn, FX.G, xr);
       ft::ypass<T, RY>(xr, yM, P);
-      ft::nb<T, RY, SW>(sn[1], R0, tx, vn);
+      ft::nb<T, RY, SW>(sn + SH * SW, R0, tx, vn);
       ft::xpass<T, RY>(vn, FX.M, xr);
       ft::ypass<T, RY>(xr, yG, P2);
 #pragma unroll
       for (int r = 0; r < RY; ++r) ft::zacc(kacc[r], P[r] + P2[r], zp.M, zs.M, zn.M);
-      ft::nb<T, RY, SW>(sn[2], R0, tx, vn);
+      ft::nb<T, RY, SW>(sn + 2 * SH * SW, R0, tx, vn);
       ft::xpass<T, RY>(vn, FX.M, xr);
       ft::ypass<T, RY>(xr, yM, P);
 #pragma unroll
@@ -582,25 +662,89 @@ __global__ void __launch_bounds__(32 * TYT) k_sources(const Geo<T> g, const SrcK
 #pragma unroll
       for (int d = 0; d < 3; ++d) Cdq[d][r] = Cdt[d][r];
     }
-    st.commit(sC[sl ^ 1], tid);
-    __syncthreads();
+    if (s < last) {
+      if (!ring.wait(s + 1)) failed = true;
+      ft::convert_box<BC, SW, SH, NT, true>(cs + ((s + 1 - ring.j0) & 1) * SH * SW, ring.at(s + 1), tid);
+    }
+    if (__syncthreads_or(failed)) {
+      if (tid == 0) ring.drain(s + 1, min(last, s + NS - 1));
+      return;
+    }
   }
+}
+
+template <typename T, int TY, int NS>
+constexpr int sources_smem() {
+  return NS * ft::Halo2<TY + 2>::BYTES + 5 * (TY + 2) * 34 * (int)sizeof(T) + NS * 8;
 }
 
 // ---------------------------------------------------------------- single-stage passes
 // Common frame of the passes whose filters reach only the node's neighbours: threads cover the
 // output tile (32 x TY), each staged field carries a one-node halo.
 
-// Stage-1 right-hand side b = sum_d G_d^T s_d (0 on the Dirichlet faces of the pressure grid).
-template <typename T, int RY, int TYT>
-__global__ void __launch_bounds__(32 * TYT) k_rhs_hs(const Geo<T> g, const Faces pf, int zc,
-                                                     const double* __restrict__ s0, const double* __restrict__ s1,
-                                                     const double* __restrict__ s2, double* __restrict__ b) {
-  constexpr int NT = 32 * TYT, TY = TYT * RY, SW = 34, SH = TY + 2;
-  __shared__ T sh[2][3][SH * SW];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
-  const int X0 = blockIdx.x * 32, Y0 = blockIdx.y * TY;
-  const int gx = X0 + tx, R0 = ty * RY;
+// Frame of the single-stage passes (filters that reach only a node's neighbours): threads cover the
+// output tile (32 x TY), and NF staged FP64 fields arrive per plane through the TMA ring with a
+// one-node halo; IC: their conversion to T runs on the integer pipe (these passes are bound by
+// memory, and the hardware conversion issues on the narrow FP64 pipe).  The macro opens the
+// kernel body up to the z loop; NN4_PASS_STEP_END closes one step.
+#define NN4_PASS_PROLOGUE(NF_, IC_)                                                                       \
+  constexpr int NT = 32 * TYT, TY = TYT * RY, SW = 34, SH = TY + 2;                                       \
+  using BF = ft::Halo1<double, SH>;                                                                       \
+  constexpr int NF = NF_, SLOT = NF_ * BF::BYTES;                                                         \
+  extern __shared__ __align__(128) unsigned char smem[];                                                  \
+  T* const cs = reinterpret_cast<T*>(smem + NS * SLOT);                                                   \
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;                                       \
+  const int X0 = blockIdx.x * 32, Y0 = blockIdx.y * TY;                                                   \
+  const int gx = X0 + tx, R0 = ty * RY;                                                                   \
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);                                                \
+  const ft::Ring<NS> ring{reinterpret_cast<uint64_t*>(cs + 2 * NF * SH * SW), smem, SLOT, z0 - 1};       \
+  const int last = z1;                                                                                    \
+  auto issue = [&](int z) {                                                                               \
+    unsigned char* d = ring.at(z);                                                                        \
+    mbar_expect_tx(ring.barrier(z), NF * BF::TX);                                                         \
+    for (int f = 0; f < NF; ++f)                                                                          \
+      tma_load_3d(d + f * BF::BYTES, &maps.m[f], X0 - 1 - BF::CO, Y0 - 1, z, ring.barrier(z));           \
+  };                                                                                                      \
+  auto convert = [&](int z, T* dst) {                                                                     \
+    const unsigned char* src = ring.at(z);                                                                \
+    for (int f = 0; f < NF; ++f) ft::convert_box<BF, SW, SH, NT, IC_>(dst + f * SH * SW, src + f * BF::BYTES, tid); \
+  };                                                                                                      \
+  if (tid == 0) ring.init();                                                                              \
+  __syncthreads();                                                                                        \
+  if (tid == 0)                                                                                           \
+    for (int z = ring.j0; z <= min(last, ring.j0 + NS - 2); ++z) issue(z);                                \
+  bool failed = !ring.wait(ring.j0);                                                                      \
+  convert(ring.j0, cs);                                                                                   \
+  if (__syncthreads_or(failed)) {                                                                         \
+    if (tid == 0) ring.drain(ring.j0, min(last, ring.j0 + NS - 2));                                       \
+    return;                                                                                               \
+  }
+
+#define NN4_PASS_STEP_BEGIN()                                                                             \
+  if (tid == 0 && s + NS - 1 <= last) issue(s + NS - 1);                                                  \
+  const T* cur = cs + ((s - ring.j0) & 1) * NF * SH * SW;
+
+#define NN4_PASS_STEP_END()                                                                               \
+  if (s < last) {                                                                                         \
+    if (!ring.wait(s + 1)) failed = true;                                                                 \
+    convert(s + 1, cs + ((s + 1 - ring.j0) & 1) * NF * SH * SW);                                          \
+  }                                                                                                       \
+  if (__syncthreads_or(failed)) {                                                                         \
+    if (tid == 0) ring.drain(s + 1, min(last, s + NS - 1));                                               \
+    return;                                                                                               \
+  }
+
+template <typename T, int TY, int NS, int NF>
+constexpr int pass_smem() {
+  return NS * NF * ft::Halo1<double, TY + 2>::BYTES + 2 * NF * (TY + 2) * 34 * (int)sizeof(T) + NS * 8;
+}
+
+// Stage-1 right-hand side b = sum_d G_d^T s_d (0 on the Dirichlet faces of the pressure grid);
+// maps: s_x, s_y, s_z.
+template <typename T, int RY, int TYT, int NS>
+__global__ void __launch_bounds__(32 * TYT) k_rhs_hs(const __grid_constant__ ft::FMaps maps, const Geo<T> g,
+                                                     const Faces pf, int zc, double* __restrict__ b) {
+  NN4_PASS_PROLOGUE(3, true)
   const Fac<T> FX = ft::facx(g, gx);
   W3<T> yM[RY], yGT[RY];
   int gy[RY];
@@ -613,36 +757,23 @@ __global__ void __launch_bounds__(32 * TYT) k_rhs_hs(const Geo<T> g, const Faces
     yGT[r] = fy.GT;
     in[r] = gx < g.nx && gy[r] < g.ny;
   }
-  const double* src[3] = {s0, s1, s2};
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
-  ft::Stage<double, SW, SH, NT> st[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    st[d].issue(src[d], g, X0 - 1, Y0 - 1, z0 - 1, tid);
-    st[d].commit(sh[0][d], tid);
-  }
-  __syncthreads();
   T A[RY][3];
 #pragma unroll
   for (int r = 0; r < RY; ++r) A[r][0] = A[r][1] = A[r][2] = T(0);
-  for (int s = z0 - 1; s <= z1; ++s) {
-    const int sl = (s - z0 + 1) & 1;
-    if (s < z1)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) st[d].issue(src[d], g, X0 - 1, Y0 - 1, s + 1, tid);
+  for (int s = ring.j0; s <= last; ++s) {
+    NN4_PASS_STEP_BEGIN()
     if (s >= 0 && s < g.nz) {
       const Fac<T> zp = ft::facz(g, s - 1), zs = ft::facz(g, s), zn = ft::facz(g, s + 1);
-      T vv[RY + 2][3], xr[RY + 2], P[RY];
-      ft::nb<T, RY, SW>(sh[sl][0], R0, tx, vv);
+      T vv[RY + 2][3], xr[RY + 2], P[RY], P1[RY];
+      ft::nb<T, RY, SW>(cur, R0, tx, vv);
       ft::xpass<T, RY>(vv, FX.GT, xr);
       ft::ypass<T, RY>(xr, yM, P);
-      T P1[RY];
-      ft::nb<T, RY, SW>(sh[sl][1], R0, tx, vv);
+      ft::nb<T, RY, SW>(cur + SH * SW, R0, tx, vv);
       ft::xpass<T, RY>(vv, FX.M, xr);
       ft::ypass<T, RY>(xr, yGT, P1);
 #pragma unroll
       for (int r = 0; r < RY; ++r) ft::zacc(A[r], P[r] + P1[r], zp.M, zs.M, zn.M);
-      ft::nb<T, RY, SW>(sh[sl][2], R0, tx, vv);
+      ft::nb<T, RY, SW>(cur + 2 * SH * SW, R0, tx, vv);
       ft::xpass<T, RY>(vv, FX.M, xr);
       ft::ypass<T, RY>(xr, yM, P);
 #pragma unroll
@@ -662,24 +793,49 @@ __global__ void __launch_bounds__(32 * TYT) k_rhs_hs(const Geo<T> g, const Faces
     }
 #pragma unroll
     for (int r = 0; r < RY; ++r) ft::zshift(A[r]);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) st[d].commit(sh[sl ^ 1][d], tid);
-    __syncthreads();
+    NN4_PASS_STEP_END()
   }
 }
 
 // Stage-3 right-hand side b = -(1/dt) sum_d [ f(rho u_d; w_d) - u_d f(rho; w_d) ] (Eq. ph_disc2),
-// rho = rho_g + (rho_l - rho_g) C formed at staging; 0 on the Dirichlet faces.
-template <typename T, int RY, int TYT>
-__global__ void __launch_bounds__(32 * TYT) k_rhs_nh(const Geo<T> g, const Faces pf, int zc, T rho_g, T rho_d,
-                                                     T inv_dt, const double* __restrict__ C,
-                                                     const double* __restrict__ u0, const double* __restrict__ u1,
-                                                     const double* __restrict__ u2, double* __restrict__ b) {
+// rho = rho_g + (rho_l - rho_g) C formed when C is converted; 0 on the Dirichlet faces.  maps:
+// C, u, v, w.
+template <typename T, int RY, int TYT, int NS>
+__global__ void __launch_bounds__(32 * TYT) k_rhs_nh(const __grid_constant__ ft::FMaps maps, const Geo<T> g,
+                                                     const Faces pf, int zc, T rho_g, T rho_d, T inv_dt,
+                                                     double* __restrict__ b) {
   constexpr int NT = 32 * TYT, TY = TYT * RY, SW = 34, SH = TY + 2;
-  __shared__ T sh[2][4][SH * SW];
+  using BF = ft::Halo1<double, SH>;
+  constexpr int NF = 4, SLOT = 4 * BF::BYTES;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* const cs = reinterpret_cast<T*>(smem + NS * SLOT);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
   const int X0 = blockIdx.x * 32, Y0 = blockIdx.y * TY;
   const int gx = X0 + tx, R0 = ty * RY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
+  const ft::Ring<NS> ring{reinterpret_cast<uint64_t*>(cs + 2 * NF * SH * SW), smem, SLOT, z0 - 1};
+  const int last = z1;
+  auto issue = [&](int z) {
+    unsigned char* d = ring.at(z);
+    mbar_expect_tx(ring.barrier(z), NF * BF::TX);
+    for (int f = 0; f < NF; ++f)
+      tma_load_3d(d + f * BF::BYTES, &maps.m[f], X0 - 1 - BF::CO, Y0 - 1, z, ring.barrier(z));
+  };
+  auto convert = [&](int z, T* dst) {
+    const unsigned char* src = ring.at(z);
+    ft::convert_box_affine<BF, SW, SH, NT, true>(dst, src, tid, rho_g, rho_d);
+    for (int f = 1; f < NF; ++f) ft::convert_box<BF, SW, SH, NT, true>(dst + f * SH * SW, src + f * BF::BYTES, tid);
+  };
+  if (tid == 0) ring.init();
+  __syncthreads();
+  if (tid == 0)
+    for (int z = ring.j0; z <= min(last, ring.j0 + NS - 2); ++z) issue(z);
+  bool failed = !ring.wait(ring.j0);
+  convert(ring.j0, cs);
+  if (__syncthreads_or(failed)) {
+    if (tid == 0) ring.drain(ring.j0, min(last, ring.j0 + NS - 2));
+    return;
+  }
   const Fac<T> FX = ft::facx(g, gx);
   W3<T> yM[RY], yG[RY];
   int gy[RY];
@@ -692,15 +848,6 @@ __global__ void __launch_bounds__(32 * TYT) k_rhs_nh(const Geo<T> g, const Faces
     yG[r] = fy.G;
     in[r] = gx < g.nx && gy[r] < g.ny;
   }
-  const double* src[4] = {C, u0, u1, u2};
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
-  ft::Stage<double, SW, SH, NT> st[4];
-#pragma unroll
-  for (int f = 0; f < 4; ++f) st[f].issue(src[f], g, X0 - 1, Y0 - 1, z0 - 1, tid);
-  st[0].commit_affine(sh[0][0], tid, rho_g, rho_d);
-#pragma unroll
-  for (int f = 1; f < 4; ++f) st[f].commit(sh[0][f], tid);
-  __syncthreads();
   // A = sum_d f(rho u_d; w_d); B_d = f(rho; w_d); node velocities of plane q
   T A[RY][3], B[3][RY][3], Uq[3][RY];
 #pragma unroll
@@ -710,16 +857,13 @@ __global__ void __launch_bounds__(32 * TYT) k_rhs_nh(const Geo<T> g, const Faces
       A[r][c] = B[0][r][c] = B[1][r][c] = B[2][r][c] = T(0);
       Uq[c][r] = T(0);
     }
-  for (int s = z0 - 1; s <= z1; ++s) {
-    const int sl = (s - z0 + 1) & 1;
-    if (s < z1)
-#pragma unroll
-      for (int f = 0; f < 4; ++f) st[f].issue(src[f], g, X0 - 1, Y0 - 1, s + 1, tid);
+  for (int s = ring.j0; s <= last; ++s) {
+    NN4_PASS_STEP_BEGIN()
     T UN[3][RY];
     if (s >= 0 && s < g.nz) {
       const Fac<T> zp = ft::facz(g, s - 1), zs = ft::facz(g, s), zn = ft::facz(g, s + 1);
       T vr[RY + 2][3];
-      ft::nb<T, RY, SW>(sh[sl][0], R0, tx, vr);
+      ft::nb<T, RY, SW>(cur, R0, tx, vr);
       T xGr[RY + 2], xMr[RY + 2], P[RY];
       ft::xpass<T, RY>(vr, FX.G, xGr);
       ft::xpass<T, RY>(vr, FX.M, xMr);
@@ -735,7 +879,7 @@ __global__ void __launch_bounds__(32 * TYT) k_rhs_nh(const Geo<T> g, const Faces
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         T vu[RY + 2][3];
-        ft::nb<T, RY, SW>(sh[sl][1 + d], R0, tx, vu);
+        ft::nb<T, RY, SW>(cur + (1 + d) * SH * SW, R0, tx, vu);
 #pragma unroll
         for (int r = 0; r < RY; ++r) UN[d][r] = vu[r + 1][1];
 #pragma unroll
@@ -778,25 +922,18 @@ __global__ void __launch_bounds__(32 * TYT) k_rhs_nh(const Geo<T> g, const Faces
         Uq[d][r] = UN[d][r];
       }
     }
-    st[0].commit_affine(sh[sl ^ 1][0], tid, rho_g, rho_d);
-#pragma unroll
-    for (int f = 1; f < 4; ++f) st[f].commit(sh[sl ^ 1][f], tid);
-    __syncthreads();
+    NN4_PASS_STEP_END()
   }
 }
 
 // Eq. vel-cor and the Stage-3 updates: u_d += -dt m^-1 f(dp; w_d) / rho (not on the no-slip faces),
-// p += dp.
-template <typename T, int RY, int TYT>
-__global__ void __launch_bounds__(32 * TYT) k_vel_correct(const Geo<T> g, const Faces vf, int zc, T rho_g, T rho_d,
-                                                          T dtT, const double* __restrict__ C,
-                                                          const double* __restrict__ dp, double* u0, double* u1,
-                                                          double* u2, double* p) {
-  constexpr int NT = 32 * TYT, TY = TYT * RY, SW = 34, SH = TY + 2;
-  __shared__ T sh[2][SH * SW];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
-  const int X0 = blockIdx.x * 32, Y0 = blockIdx.y * TY;
-  const int gx = X0 + tx, R0 = ty * RY;
+// p += dp.  maps: dp.
+template <typename T, int RY, int TYT, int NS>
+__global__ void __launch_bounds__(32 * TYT) k_vel_correct(const __grid_constant__ ft::FMaps maps, const Geo<T> g,
+                                                          const Faces vf, int zc, T rho_g, T rho_d, T dtT,
+                                                          const double* __restrict__ C, const double* __restrict__ dp,
+                                                          double* u0, double* u1, double* u2, double* p) {
+  NN4_PASS_PROLOGUE(1, true)
   const Fac<T> FX = ft::facx(g, gx);
   W3<T> yM[RY], yG[RY];
   T ly[RY];
@@ -811,24 +948,21 @@ __global__ void __launch_bounds__(32 * TYT) k_vel_correct(const Geo<T> g, const 
     ly[r] = fy.lump;
     in[r] = gx < g.nx && gy[r] < g.ny;
   }
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
-  ft::Stage<double, SW, SH, NT> st;
-  st.issue(dp, g, X0 - 1, Y0 - 1, z0 - 1, tid);
-  st.commit(sh[0], tid);
-  __syncthreads();
   T A[3][RY][3];
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
     for (int r = 0; r < RY; ++r) A[d][r][0] = A[d][r][1] = A[d][r][2] = T(0);
   double* uu[3] = {u0, u1, u2};
-  for (int s = z0 - 1; s <= z1; ++s) {
-    const int sl = (s - z0 + 1) & 1;
-    if (s < z1) st.issue(dp, g, X0 - 1, Y0 - 1, s + 1, tid);
+  double cr[RY], dr[RY], ur[3][RY];  // prefetched C, dp and u of plane s - 1
+#pragma unroll
+  for (int r = 0; r < RY; ++r) cr[r] = dr[r] = ur[0][r] = ur[1][r] = ur[2][r] = 0.0;
+  for (int s = ring.j0; s <= last; ++s) {
+    NN4_PASS_STEP_BEGIN()
     if (s >= 0 && s < g.nz) {
       const Fac<T> zp = ft::facz(g, s - 1), zs = ft::facz(g, s), zn = ft::facz(g, s + 1);
       T vv[RY + 2][3], xG[RY + 2], xM[RY + 2], P[RY];
-      ft::nb<T, RY, SW>(sh[sl], R0, tx, vv);
+      ft::nb<T, RY, SW>(cur, R0, tx, vv);
       ft::xpass<T, RY>(vv, FX.G, xG);
       ft::xpass<T, RY>(vv, FX.M, xM);
       ft::ypass<T, RY>(xG, yM, P);
@@ -849,28 +983,36 @@ __global__ void __launch_bounds__(32 * TYT) k_vel_correct(const Geo<T> g, const 
         if (!in[r]) continue;
         const long long o = (long long)q * g.plane + (long long)gy[r] * g.pitch + gx;
         if (!on_face(vf, gx, gy[r], q, g.nx, g.ny, g.nz)) {
-          const double c = __ldg(C + o);
           if constexpr (sizeof(T) == 8) {
-            const double rho = rho_g + rho_d * c;
+            const double rho = rho_g + rho_d * cr[r];
             const double f = -dtT / (FX.lump * ly[r] * lz * rho);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) uu[d][o] += f * A[d][r][0];
+            for (int d = 0; d < 3; ++d) uu[d][o] = ur[d][r] + f * A[d][r][0];
           } else {
-            const T rho = rho_g + rho_d * ft::from64<T>(c);
+            const T rho = rho_g + rho_d * ft::from64<T>(cr[r]);
             const T f = -dtT / (FX.lump * ly[r] * lz * rho);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) uu[d][o] += ft::to64(f * A[d][r][0]);
+            for (int d = 0; d < 3; ++d) uu[d][o] = ur[d][r] + ft::to64(f * A[d][r][0]);
           }
         }
-        if (p) p[o] += __ldg(dp + o);
+        if (p) p[o] += dr[r];
       }
+    }
+    // prefetch C, dp and u of plane s (emitted at the next step)
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      const bool ok = in[r] && s >= z0 && s < z1;
+      const long long o = (long long)s * g.plane + (long long)gy[r] * g.pitch + gx;
+      cr[r] = ok ? __ldg(C + o) : 0.0;
+      dr[r] = ok ? __ldg(dp + o) : 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ur[d][r] = ok ? uu[d][o] : 0.0;
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
       for (int r = 0; r < RY; ++r) ft::zshift(A[d][r]);
-    st.commit(sh[sl ^ 1], tid);
-    __syncthreads();
+    NN4_PASS_STEP_END()
   }
 }
 
@@ -885,17 +1027,37 @@ struct MomK {
   T rho_g, rho_d, mu_g, mu_d;  // rho = rho_g + rho_d C, mu = mu_g + mu_d C
 };
 
-template <typename T, int RY, int TYT>
-__global__ void __launch_bounds__(32 * TYT) k_mom_coef(const Geo<T> g, const MomK<T> p, int zc, int comp,
-                                                       const double* __restrict__ C, const double* __restrict__ uh0,
-                                                       const double* __restrict__ uh1, const double* __restrict__ uh2,
-                                                       T* __restrict__ kout) {
+template <typename T, int RY, int TYT, int NS>
+__global__ void __launch_bounds__(32 * TYT) k_mom_coef(const __grid_constant__ ft::FMaps maps, const Geo<T> g,
+                                                       const MomK<T> p, int zc, const double* __restrict__ C,
+                                                       const double* __restrict__ uh0, const double* __restrict__ uh1,
+                                                       const double* __restrict__ uh2, T* __restrict__ kout) {
   constexpr int NT = 32 * TYT, TY = TYT * RY, SW = 34, SH = TY + 2;
-  __shared__ T sP[2][SH * SW];
-  __shared__ T sg[SH * SW];
+  using BC = ft::Halo2<SH>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* const cs = reinterpret_cast<T*>(smem + NS * BC::BYTES);  // compute slots [2][SH * SW] of psi
+  T* const sg = cs + 2 * SH * SW;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
   const int X0 = blockIdx.x * 30, Y0 = blockIdx.y * (TY - 2);
   const int gx = X0 - 1 + tx, R0 = ty * RY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
+  ft::Ring<NS> ring{reinterpret_cast<uint64_t*>(sg + SH * SW), smem, BC::BYTES, z0 - 2};
+  const int last = z1 + 1;
+  auto issue = [&](int z) {
+    mbar_expect_tx(ring.barrier(z), BC::TX);
+    tma_load_3d(ring.at(z), &maps.m[0], X0 - 2, Y0 - 2, z, ring.barrier(z));
+  };
+  if (tid == 0) ring.init();
+  for (int i = tid; i < SH * SW; i += NT) sg[i] = T(0);
+  __syncthreads();
+  if (tid == 0)
+    for (int z = ring.j0; z <= min(last, ring.j0 + NS - 2); ++z) issue(z);
+  bool failed = !ring.wait(ring.j0);
+  ft::convert_box<BC, SW, SH, NT>(cs, ring.at(ring.j0), tid);
+  if (__syncthreads_or(failed)) {
+    if (tid == 0) ring.drain(ring.j0, min(last, ring.j0 + NS - 2));
+    return;
+  }
   const Fac<T> FX = ft::facx(g, gx);
   W3<T> yM[RY], yG[RY];
   T ly[RY];
@@ -911,28 +1073,23 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_coef(const Geo<T> g, const Mom
     in[r] = gx >= 0 && gx < g.nx && gy[r] >= 0 && gy[r] < g.ny;
     outp[r] = in[r] && tx >= 1 && tx <= 30 && R0 + r >= 1 && R0 + r <= TY - 2;
   }
-  for (int i = tid; i < SH * SW; i += NT) sg[i] = T(0);
   const double* uh[3] = {uh0, uh1, uh2};
-  const double* psi = uh[comp];
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
-  ft::Stage<double, SW, SH, NT> st;
-  st.issue(psi, g, X0 - 2, Y0 - 2, z0 - 2, tid);
-  st.commit(sP[0], tid);
-  __syncthreads();
-
   T gacc[3][RY][3], aacc[RY][3], Pdq[3][RY], gq[RY], Uq[3][RY];
+  double Ur[3][RY], cr[RY];  // prefetched u^{n+1/2} of plane s - 1 and C of plane s - 2
 #pragma unroll
   for (int r = 0; r < RY; ++r) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       gacc[0][r][c] = gacc[1][r][c] = gacc[2][r][c] = aacc[r][c] = T(0);
       Pdq[c][r] = Uq[c][r] = T(0);
+      Ur[c][r] = 0.0;
     }
     gq[r] = T(0);
+    cr[r] = 0.0;
   }
-  for (int s = z0 - 2; s <= z1 + 1; ++s) {
-    const int sl = (s - z0) & 1;
-    if (s <= z1) st.issue(psi, g, X0 - 2, Y0 - 2, s + 1, tid);
+  for (int s = ring.j0; s <= last; ++s) {
+    if (tid == 0 && s + NS - 1 <= last) issue(s + NS - 1);
+    const T* cur = cs + ((s - ring.j0) & 1) * SH * SW;
     const int t = s - 1, q = s - 2;
     const bool tin = t >= 0 && t < g.nz;
     const bool emit = q >= z0 && q < z1;
@@ -940,18 +1097,13 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_coef(const Geo<T> g, const Mom
     double c64[RY];
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
-      if (tin && in[r]) {
-        const long long o = (long long)t * g.plane + (long long)gy[r] * g.pitch + gx;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) Ut[d][r] = ft::load_as<T>(uh[d] + o);
-      } else {
-        Ut[0][r] = Ut[1][r] = Ut[2][r] = T(0);
-      }
-      c64[r] = (emit && outp[r]) ? __ldg(C + (long long)q * g.plane + (long long)gy[r] * g.pitch + gx) : 0.0;
+      for (int d = 0; d < 3; ++d) Ut[d][r] = ft::from64<T>(Ur[d][r]);
+      c64[r] = cr[r];
     }
     if (s >= 0 && s < g.nz) {
       T vv[RY + 2][3], xG[RY + 2], xM[RY + 2], GM[RY], MG[RY], MM[RY];
-      ft::nb<T, RY, SW>(sP[sl], R0, tx, vv);
+      ft::nb<T, RY, SW>(cur, R0, tx, vv);
       ft::xpass<T, RY>(vv, FX.G, xG);
       ft::xpass<T, RY>(vv, FX.M, xM);
       ft::ypass<T, RY>(xG, yM, GM);
@@ -982,6 +1134,15 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_coef(const Geo<T> g, const Mom
 #pragma unroll
         for (int d = 0; d < 3; ++d) ft::zshift(gacc[d][r]);
       }
+    }
+    // prefetch u^{n+1/2} of plane s and C of plane t (used at the next step)
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      const bool ok = in[r] && s >= 0 && s < g.nz;
+      const long long o = (long long)s * g.plane + (long long)gy[r] * g.pitch + gx;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Ur[d][r] = ok ? __ldg(uh[d] + o) : 0.0;
+      cr[r] = (outp[r] && t >= z0 && t < z1) ? __ldg(C + o - g.plane) : 0.0;
     }
     __syncthreads();
     if (tin) {
@@ -1025,8 +1186,14 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_coef(const Geo<T> g, const Mom
       }
       gq[r] = gt[r];
     }
-    st.commit(sP[sl ^ 1], tid);
-    __syncthreads();
+    if (s < last) {
+      if (!ring.wait(s + 1)) failed = true;
+      ft::convert_box<BC, SW, SH, NT>(cs + ((s + 1 - ring.j0) & 1) * SH * SW, ring.at(s + 1), tid);
+    }
+    if (__syncthreads_or(failed)) {
+      if (tid == 0) ring.drain(s + 1, min(last, s + NS - 1));
+      return;
+    }
   }
 }
 
@@ -1034,19 +1201,50 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_coef(const Geo<T> g, const Mom
 // + f(p; w_c) - f(s_c; w_m) (Eq. Petrov-u/v/w with the isotropic L = w_lap of Eq. k-T), then
 // psi~ = psi^n - dt s~ / (m rho) (0 on the no-slip faces; Eq. velocity-1 with sigma = 0) and
 // psi^{n+1/2} = (psi^n + psi~) / 2.
-template <typename T, int RY, int TYT>
-__global__ void __launch_bounds__(32 * TYT) k_mom_update(const Geo<T> g, const MomK<T> p, const Faces vf, int zc,
-                                                         int comp, double dt, T dtT, const double* __restrict__ C,
+template <typename T, int RY, int TYT, int NS>
+__global__ void __launch_bounds__(32 * TYT) k_mom_update(const __grid_constant__ ft::FMaps maps, const Geo<T> g,
+                                                         const MomK<T> p, const Faces vf, int zc, int comp, double dt,
+                                                         T dtT, const double* __restrict__ C,
                                                          const double* __restrict__ uh0, const double* __restrict__ uh1,
-                                                         const double* __restrict__ uh2, const T* __restrict__ kpsi,
-                                                         const double* __restrict__ pt, const double* __restrict__ src,
-                                                         const double* __restrict__ un, double* __restrict__ ut,
-                                                         double* __restrict__ uh_next) {
+                                                         const double* __restrict__ uh2, const double* __restrict__ un,
+                                                         double* __restrict__ ut, double* __restrict__ uh_next) {
   constexpr int NT = 32 * TYT, TY = TYT * RY, SW = 34, SH = TY + 2;
-  __shared__ T sh[2][4][SH * SW];  // psi, k, p, s
+  using BD = ft::Halo1<double, SH>;
+  using BK = ft::Halo1<T, SH>;
+  // slot: psi, p, s (FP64), then k (type T)
+  constexpr int NF = 4, SLOT = 3 * BD::BYTES + BK::BYTES;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* const cs = reinterpret_cast<T*>(smem + NS * SLOT);  // compute slots [2][4][SH * SW]: psi, k, p, s
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
   const int X0 = blockIdx.x * 32, Y0 = blockIdx.y * TY;
   const int gx = X0 + tx, R0 = ty * RY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
+  ft::Ring<NS> ring{reinterpret_cast<uint64_t*>(cs + 2 * NF * SH * SW), smem, SLOT, z0 - 1};
+  const int last = z1;
+  auto issue = [&](int z) {
+    unsigned char* d = ring.at(z);
+    mbar_expect_tx(ring.barrier(z), 3 * BD::TX + BK::TX);
+    for (int f = 0; f < 3; ++f)
+      tma_load_3d(d + f * BD::BYTES, &maps.m[f], X0 - 1 - BD::CO, Y0 - 1, z, ring.barrier(z));
+    tma_load_3d(d + 3 * BD::BYTES, &maps.m[3], X0 - 1 - BK::CO, Y0 - 1, z, ring.barrier(z));
+  };
+  auto convert = [&](int z, T* dst) {
+    const unsigned char* src = ring.at(z);
+    ft::convert_box<BD, SW, SH, NT>(dst, src, tid);                                  // psi
+    ft::convert_box<BK, SW, SH, NT>(dst + SH * SW, src + 3 * BD::BYTES, tid);       // k
+    ft::convert_box<BD, SW, SH, NT>(dst + 2 * SH * SW, src + BD::BYTES, tid);       // p
+    ft::convert_box<BD, SW, SH, NT>(dst + 3 * SH * SW, src + 2 * BD::BYTES, tid);   // s
+  };
+  if (tid == 0) ring.init();
+  __syncthreads();
+  if (tid == 0)
+    for (int z = ring.j0; z <= min(last, ring.j0 + NS - 2); ++z) issue(z);
+  bool failed = !ring.wait(ring.j0);
+  convert(ring.j0, cs);
+  if (__syncthreads_or(failed)) {
+    if (tid == 0) ring.drain(ring.j0, min(last, ring.j0 + NS - 2));
+    return;
+  }
   const Fac<T> FX = ft::facx(g, gx);
   W3<T> yM[RY], yG[RY], yK[RY];
   T ly[RY];
@@ -1063,53 +1261,24 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_update(const Geo<T> g, const M
     in[r] = gx < g.nx && gy[r] < g.ny;
   }
   const double* uh[3] = {uh0, uh1, uh2};
-  const double* psi = uh[comp];
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.nz);
-  ft::Stage<double, SW, SH, NT> stP, stp, sts;
-  ft::Stage<T, SW, SH, NT> stk;
-  stP.issue(psi, g, X0 - 1, Y0 - 1, z0 - 1, tid);
-  stk.issue(kpsi, g, X0 - 1, Y0 - 1, z0 - 1, tid);
-  stp.issue(pt, g, X0 - 1, Y0 - 1, z0 - 1, tid);
-  sts.issue(src, g, X0 - 1, Y0 - 1, z0 - 1, tid);
-  stP.commit(sh[0][0], tid);
-  stk.commit(sh[0][1], tid);
-  stp.commit(sh[0][2], tid);
-  sts.commit(sh[0][3], tid);
-  __syncthreads();
   // accumulators: raw gradient of psi (3), A = (1/2) L(k psi) + f(p; w_c) - f(s; w_m), L psi, L k
   T Acc[6][RY][3], Pq[RY], Kq[RY];
+  double Ur[3][RY], cr[RY], nr[RY];  // prefetched u^{n+1/2}, C and u^n_c of plane s - 1
 #pragma unroll
   for (int a = 0; a < 6; ++a)
 #pragma unroll
     for (int r = 0; r < RY; ++r) Acc[a][r][0] = Acc[a][r][1] = Acc[a][r][2] = T(0);
 #pragma unroll
-  for (int r = 0; r < RY; ++r) Pq[r] = Kq[r] = T(0);
+  for (int r = 0; r < RY; ++r) {
+    Pq[r] = Kq[r] = T(0);
+    Ur[0][r] = Ur[1][r] = Ur[2][r] = cr[r] = nr[r] = 0.0;
+  }
 
-  for (int s = z0 - 1; s <= z1; ++s) {
-    const int sl = (s - z0 + 1) & 1;
-    if (s < z1) {
-      stP.issue(psi, g, X0 - 1, Y0 - 1, s + 1, tid);
-      stk.issue(kpsi, g, X0 - 1, Y0 - 1, s + 1, tid);
-      stp.issue(pt, g, X0 - 1, Y0 - 1, s + 1, tid);
-      sts.issue(src, g, X0 - 1, Y0 - 1, s + 1, tid);
-    }
+  for (int s = ring.j0; s <= last; ++s) {
+    if (tid == 0 && s + NS - 1 <= last) issue(s + NS - 1);
+    const T* cur = cs + ((s - ring.j0) & 1) * NF * SH * SW;
     const int q = s - 1;
     const bool emit = q >= z0;
-    T U[3][RY];
-    double c64[RY], un64[RY];
-#pragma unroll
-    for (int r = 0; r < RY; ++r) {
-      if (emit && in[r]) {
-        const long long o = (long long)q * g.plane + (long long)gy[r] * g.pitch + gx;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) U[d][r] = ft::load_as<T>(uh[d] + o);
-        c64[r] = __ldg(C + o);
-        un64[r] = __ldg(un + o);
-      } else {
-        U[0][r] = U[1][r] = U[2][r] = T(0);
-        c64[r] = un64[r] = 0.0;
-      }
-    }
     T PN[RY], KN[RY];
     if (s >= 0 && s < g.nz) {
       const Fac<T> zp = ft::facz(g, s - 1), zs = ft::facz(g, s), zn = ft::facz(g, s + 1);
@@ -1117,7 +1286,7 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_update(const Geo<T> g, const M
       {
         // psi: raw gradient and L psi
         T v[RY + 2][3], xG[RY + 2], xM[RY + 2], xK[RY + 2];
-        ft::nb<T, RY, SW>(sh[sl][0], R0, tx, v);
+        ft::nb<T, RY, SW>(cur, R0, tx, v);
 #pragma unroll
         for (int r = 0; r < RY; ++r) PN[r] = v[r + 1][1];
         ft::xpass<T, RY>(v, FX.G, xG);
@@ -1141,7 +1310,7 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_update(const Geo<T> g, const M
         for (int r = 0; r < RY; ++r) ft::zacc(Acc[4][r], P[r] + P2[r], zp.M, zs.M, zn.M);
         // k and k psi: L k and (1/2) L(k psi)
         T vk[RY + 2][3];
-        ft::nb<T, RY, SW>(sh[sl][1], R0, tx, vk);
+        ft::nb<T, RY, SW>(cur + SH * SW, R0, tx, vk);
 #pragma unroll
         for (int r = 0; r < RY; ++r) KN[r] = vk[r + 1][1];
         ft::xpass<T, RY>(vk, FX.M, xM);
@@ -1170,7 +1339,7 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_update(const Geo<T> g, const M
       {
         // f(p; w_c) - f(s; w_m)
         T v[RY + 2][3], xr[RY + 2];
-        ft::nb<T, RY, SW>(sh[sl][2], R0, tx, v);
+        ft::nb<T, RY, SW>(cur + 2 * SH * SW, R0, tx, v);
         ft::xpass<T, RY>(v, comp == 0 ? FX.G : FX.M, xr);
         ft::ypass<T, RY>(xr, comp == 1 ? yG : yM, P);
         const W3<T>& wp = comp == 2 ? zp.G : zp.M;
@@ -1178,7 +1347,7 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_update(const Geo<T> g, const M
         const W3<T>& wn = comp == 2 ? zn.G : zn.M;
 #pragma unroll
         for (int r = 0; r < RY; ++r) ft::zacc(Acc[3][r], P[r], wp, ws, wn);
-        ft::nb<T, RY, SW>(sh[sl][3], R0, tx, v);
+        ft::nb<T, RY, SW>(cur + 3 * SH * SW, R0, tx, v);
         ft::xpass<T, RY>(v, FX.M, xr);
         ft::ypass<T, RY>(xr, yM, P);
 #pragma unroll
@@ -1194,26 +1363,38 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_update(const Geo<T> g, const M
       for (int r = 0; r < RY; ++r) {
         if (!in[r]) continue;
         const long long o = (long long)q * g.plane + (long long)gy[r] * g.pitch + gx;
-        const T c = ft::from64<T>(c64[r]);
+        const T c = ft::from64<T>(cr[r]);
         const T rho = p.rho_g + p.rho_d * c;
-        const T sv = rho * (U[0][r] * Acc[0][r][0] + U[1][r] * Acc[1][r][0] + U[2][r] * Acc[2][r][0]) + Acc[3][r][0] +
-                     T(0.5) * (Kq[r] * Acc[4][r][0] - Pq[r] * Acc[5][r][0]);
+        const T sv = rho * (ft::from64<T>(Ur[0][r]) * Acc[0][r][0] + ft::from64<T>(Ur[1][r]) * Acc[1][r][0] +
+                            ft::from64<T>(Ur[2][r]) * Acc[2][r][0]) +
+                     Acc[3][r][0] + T(0.5) * (Kq[r] * Acc[4][r][0] - Pq[r] * Acc[5][r][0]);
+        const double un64 = nr[r];
         if (on_face(vf, gx, gy[r], q, g.nx, g.ny, g.nz)) {
           ut[o] = 0.0;
-          if (uh_next) uh_next[o] = 0.5 * un64[r];
+          if (uh_next) uh_next[o] = 0.5 * un64;
         } else {
           const T m = FX.lump * ly[r] * lz;
           if constexpr (sizeof(T) == 8) {
-            const double v = un64[r] - dt * sv / (m * rho);
+            const double v = un64 - dt * sv / (m * rho);
             ut[o] = v;
-            if (uh_next) uh_next[o] = 0.5 * (un64[r] + v);
+            if (uh_next) uh_next[o] = 0.5 * (un64 + v);
           } else {
             const T delta = -dtT * sv / (m * rho);
-            ut[o] = un64[r] + ft::to64(delta);
-            if (uh_next) uh_next[o] = un64[r] + ft::to64(T(0.5) * delta);
+            ut[o] = un64 + ft::to64(delta);
+            if (uh_next) uh_next[o] = un64 + ft::to64(T(0.5) * delta);
           }
         }
       }
+    }
+    // prefetch u^{n+1/2}, C and u^n_c of plane s (emitted at the next step)
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      const bool ok = in[r] && s >= z0 && s < z1;
+      const long long o = (long long)s * g.plane + (long long)gy[r] * g.pitch + gx;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) Ur[d][r] = ok ? __ldg(uh[d] + o) : 0.0;
+      cr[r] = ok ? __ldg(C + o) : 0.0;
+      nr[r] = ok ? __ldg(un + o) : 0.0;
     }
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
@@ -1222,12 +1403,21 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_update(const Geo<T> g, const M
       Pq[r] = PN[r];
       Kq[r] = KN[r];
     }
-    stP.commit(sh[sl ^ 1][0], tid);
-    stk.commit(sh[sl ^ 1][1], tid);
-    stp.commit(sh[sl ^ 1][2], tid);
-    sts.commit(sh[sl ^ 1][3], tid);
-    __syncthreads();
+    if (s < last) {
+      if (!ring.wait(s + 1)) failed = true;
+      convert(s + 1, cs + ((s + 1 - ring.j0) & 1) * NF * SH * SW);
+    }
+    if (__syncthreads_or(failed)) {
+      if (tid == 0) ring.drain(s + 1, min(last, s + NS - 1));
+      return;
+    }
   }
+}
+
+template <typename T, int TY, int NS>
+constexpr int mom_update_smem() {
+  return NS * (3 * ft::Halo1<double, TY + 2>::BYTES + ft::Halo1<T, TY + 2>::BYTES) +
+         2 * 4 * (TY + 2) * 34 * (int)sizeof(T) + NS * 8;
 }
 
 // ---------------------------------------------------------------- reductions
@@ -1298,12 +1488,12 @@ struct Shape<double> {
   static constexpr int RY = 2, TYT = 8;
 };
 
-// z planes per block: enough blocks for two waves of 152 SMs, at most 32 planes per block
+// z planes per block: enough blocks for two waves of 152 SMs, at most 64 planes per block
 int zchunk_for(long long tiles_xy, int nz) {
   const long long want = 2LL * 152 * 2;
   long long chunks = (want + tiles_xy - 1) / tiles_xy;
   int zc = (int)((nz + chunks - 1) / chunks);
-  zc = std::max(4, std::min(32, zc));
+  zc = std::max(4, std::min(64, zc));
   return zc;
 }
 
@@ -1361,19 +1551,41 @@ MomK<T> mom_k(const nn4_flow_params* fp, const nn4_grid* g) {
   return k;
 }
 
+// dynamic shared memory of a kernel above the default 48 KB
+template <typename K>
+int allow_smem(K kern, int bytes) {
+  return check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+                    "cudaFuncSetAttribute(flow kernel)");
+}
+
+// tensor map of an FP64 or FP32 field on grid g (row pitch g->pitch elements) with box bw x bh
+bool fmap(CUtensorMap* m, const nn4_grid* g, bool f64, const void* base, int bw, int bh) {
+  return make_tmap_3d(m, f64 ? NN4_F64 : NN4_F32, base, g->n[0], g->n[1], g->n[2], g->pitch, bw, bh);
+}
+
+constexpr int kRing = 4;  // raw plane slots of the flow kernels (3 planes in flight)
+
 // the VOF step on a scratch of three coefficient fields (elements f apart)
 template <typename T>
 int vof_launch(const nn4_grid* g, const nn4_vof_params* p, const double* C, const double* u, const double* v,
                const double* w, double* s_C, double* C_next, void* scratch, size_t f, cudaStream_t s) {
-  constexpr int RY = Shape<T>::RY, TYT = Shape<T>::TYT, TY = RY * TYT;
+  constexpr int RY = Shape<T>::RY, TYT = Shape<T>::TYT, TY = RY * TYT, SH = TY + 2;
   const Geo<T> G = make_geo<T>(g);
   T* k = static_cast<T*>(scratch);
+  ft::FMaps ma{}, mb{};
+  bool ok = fmap(&ma.m[0], g, true, C, ft::Halo2<SH>::BW, SH) && fmap(&mb.m[0], g, true, C, ft::Halo1<double, SH>::BW, SH);
+  for (int d = 0; d < 3; ++d) ok = ok && fmap(&mb.m[1 + d], g, sizeof(T) == 8, k + d * f, ft::Halo1<T, SH>::BW, SH);
+  if (!ok) return set_error(NN4_ECUDA, "tensor map encode failed (VOF)");
+  auto ka = k_vof_coef<T, RY, TYT, kRing>;
+  auto kb = k_vof_update<T, RY, TYT, kRing>;
+  constexpr int sa = vof_coef_smem<T, TY, kRing>(), sb = vof_update_smem<T, TY, kRing>();
+  int rc;
+  if ((rc = allow_smem(ka, sa)) || (rc = allow_smem(kb, sb))) return rc;
   int zc = 0;
   dim3 ga = grid_out<T>(g, 30, TY - 2, &zc);
-  k_vof_coef<T, RY, TYT><<<ga, dim3(32, TYT), 0, s>>>(G, vof_k<T>(p, g), zc, C, u, v, w, k, k + f, k + 2 * f);
+  ka<<<ga, dim3(32, TYT), sa, s>>>(ma, G, vof_k<T>(p, g), zc, C, u, v, w, k, k + f, k + 2 * f);
   dim3 gb = grid_out<T>(g, 32, TY, &zc);
-  k_vof_update<T, RY, TYT><<<gb, dim3(32, TYT), 0, s>>>(G, p->dt, (T)p->dt, zc, C, k, k + f, k + 2 * f, u, v, w, s_C,
-                                                       C_next);
+  kb<<<gb, dim3(32, TYT), sb, s>>>(mb, G, p->dt, (T)p->dt, zc, C, u, v, w, s_C, C_next);
   return check_cuda(cudaGetLastError(), "VOF kernels");
 }
 
@@ -1406,9 +1618,16 @@ int sources_launch(const nn4_grid* g, const nn4_flow_params* fp, const double* C
   p.sigma = (T)fp->sigma_t;
   p.grho_g = (T)(fp->g * fp->rho_g);
   p.grho_d = (T)(fp->g * (fp->rho_l - fp->rho_g));
+  constexpr int SH = TY + 2;
+  ft::FMaps m{};
+  if (!fmap(&m.m[0], g, true, C, ft::Halo2<SH>::BW, SH)) return set_error(NN4_ECUDA, "tensor map encode failed (sources)");
+  auto kern = k_sources<T, RY, TYT, kRing>;
+  constexpr int sm = sources_smem<T, TY, kRing>();
+  int rc;
+  if ((rc = allow_smem(kern, sm))) return rc;
   int zc = 0;
   dim3 ga = grid_out<T>(g, 30, TY - 2, &zc);
-  k_sources<T, RY, TYT><<<ga, dim3(32, TYT), 0, st>>>(make_geo<T>(g), p, zc, C, s0, s1, s2, kappa);
+  kern<<<ga, dim3(32, TYT), sm, st>>>(m, make_geo<T>(g), p, zc, C, s0, s1, s2, kappa);
   return check_cuda(cudaGetLastError(), "momentum sources");
 }
 
@@ -1416,9 +1635,19 @@ template <typename T>
 int rhs_hs_launch(const nn4_grid* g, const double* s0, const double* s1, const double* s2, double* b,
                          cudaStream_t st) {
   constexpr int RY = Shape<T>::RY, TYT = Shape<T>::TYT, TY = RY * TYT;
+  constexpr int SH = TY + 2;
+  ft::FMaps m{};
+  const double* src[3] = {s0, s1, s2};
+  for (int d = 0; d < 3; ++d)
+    if (!fmap(&m.m[d], g, true, src[d], ft::Halo1<double, SH>::BW, SH))
+      return set_error(NN4_ECUDA, "tensor map encode failed (stage-1 rhs)");
+  auto kern = k_rhs_hs<T, RY, TYT, kRing>;
+  constexpr int sm = pass_smem<T, TY, kRing, 3>();
+  int rc;
+  if ((rc = allow_smem(kern, sm))) return rc;
   int zc = 0;
   dim3 gb = grid_out<T>(g, 32, TY, &zc);
-  k_rhs_hs<T, RY, TYT><<<gb, dim3(32, TYT), 0, st>>>(make_geo<T>(g), faces_of(g), zc, s0, s1, s2, b);
+  kern<<<gb, dim3(32, TYT), sm, st>>>(m, make_geo<T>(g), faces_of(g), zc, b);
   return check_cuda(cudaGetLastError(), "stage-1 rhs");
 }
 
@@ -1426,10 +1655,20 @@ template <typename T>
 int rhs_nh_launch(const nn4_grid* g, const nn4_flow_params* fp, const double* C, const double* u,
                          const double* v, const double* w, double* b, cudaStream_t st) {
   constexpr int RY = Shape<T>::RY, TYT = Shape<T>::TYT, TY = RY * TYT;
+  constexpr int SH = TY + 2;
+  ft::FMaps m{};
+  const double* src[4] = {C, u, v, w};
+  for (int d = 0; d < 4; ++d)
+    if (!fmap(&m.m[d], g, true, src[d], ft::Halo1<double, SH>::BW, SH))
+      return set_error(NN4_ECUDA, "tensor map encode failed (stage-3 rhs)");
+  auto kern = k_rhs_nh<T, RY, TYT, kRing>;
+  constexpr int sm = pass_smem<T, TY, kRing, 4>();
+  int rc;
+  if ((rc = allow_smem(kern, sm))) return rc;
   int zc = 0;
   dim3 gb = grid_out<T>(g, 32, TY, &zc);
-  k_rhs_nh<T, RY, TYT><<<gb, dim3(32, TYT), 0, st>>>(make_geo<T>(g), faces_of(g), zc, (T)fp->rho_g,
-                                                     (T)(fp->rho_l - fp->rho_g), (T)(1.0 / fp->dt), C, u, v, w, b);
+  kern<<<gb, dim3(32, TYT), sm, st>>>(m, make_geo<T>(g), faces_of(g), zc, (T)fp->rho_g, (T)(fp->rho_l - fp->rho_g),
+                                      (T)(1.0 / fp->dt), b);
   return check_cuda(cudaGetLastError(), "stage-3 rhs");
 }
 
@@ -1437,10 +1676,18 @@ template <typename T>
 int vel_launch(const nn4_grid* g, const nn4_flow_params* fp, const double* C, const double* dp, double* u,
                       double* v, double* w, double* p_nh, cudaStream_t st) {
   constexpr int RY = Shape<T>::RY, TYT = Shape<T>::TYT, TY = RY * TYT;
+  constexpr int SH = TY + 2;
+  ft::FMaps m{};
+  if (!fmap(&m.m[0], g, true, dp, ft::Halo1<double, SH>::BW, SH))
+    return set_error(NN4_ECUDA, "tensor map encode failed (velocity correction)");
+  auto kern = k_vel_correct<T, RY, TYT, kRing>;
+  constexpr int sm = pass_smem<T, TY, kRing, 1>();
+  int rc;
+  if ((rc = allow_smem(kern, sm))) return rc;
   int zc = 0;
   dim3 gb = grid_out<T>(g, 32, TY, &zc);
-  k_vel_correct<T, RY, TYT><<<gb, dim3(32, TYT), 0, st>>>(make_geo<T>(g), faces_of(g), zc, (T)fp->rho_g,
-                                                          (T)(fp->rho_l - fp->rho_g), (T)fp->dt, C, dp, u, v, w, p_nh);
+  kern<<<gb, dim3(32, TYT), sm, st>>>(m, make_geo<T>(g), faces_of(g), zc, (T)fp->rho_g, (T)(fp->rho_l - fp->rho_g),
+                                      (T)fp->dt, C, dp, u, v, w, p_nh);
   return check_cuda(cudaGetLastError(), "velocity correction");
 }
 
@@ -1453,17 +1700,33 @@ int predict_launch(const nn4_grid* g, const nn4_flow_params* fp, const double* C
   const MomK<T> mk = mom_k<T>(fp, g);
   const size_t f = (size_t)g->pitch * g->n[1] * g->n[2];
   T* k = static_cast<T*>(workspace);
+  constexpr int SH = TY + 2;
+  auto ka = k_mom_coef<T, RY, TYT, kRing>;
+  auto kb = k_mom_update<T, RY, TYT, kRing>;
+  constexpr int sa = vof_coef_smem<T, TY, kRing>(), sb = mom_update_smem<T, TY, kRing>();
+  int rc;
+  if ((rc = allow_smem(ka, sa)) || (rc = allow_smem(kb, sb))) return rc;
   int zc = 0;
   dim3 ga = grid_out<T>(g, 30, TY - 2, &zc);
-  for (int c = 0; c < 3; ++c)
-    k_mom_coef<T, RY, TYT><<<ga, dim3(32, TYT), 0, st>>>(G, mk, zc, c, C, uh[0], uh[1], uh[2], k + c * f);
+  for (int c = 0; c < 3; ++c) {
+    ft::FMaps m{};
+    if (!fmap(&m.m[0], g, true, uh[c], ft::Halo2<SH>::BW, SH))
+      return set_error(NN4_ECUDA, "tensor map encode failed (predictor)");
+    ka<<<ga, dim3(32, TYT), sa, st>>>(m, G, mk, zc, C, uh[0], uh[1], uh[2], k + c * f);
+  }
   int zc2 = 0;
   dim3 gb = grid_out<T>(g, 32, TY, &zc2);
   const Faces vf = faces_of(g);
-  for (int c = 0; c < 3; ++c)
-    k_mom_update<T, RY, TYT><<<gb, dim3(32, TYT), 0, st>>>(G, mk, vf, zc2, c, fp->dt, (T)fp->dt, C, uh[0], uh[1],
-                                                           uh[2], k + c * f, p, src[c], un[c], ut[c],
-                                                           uh_next ? uh_next[c] : nullptr);
+  for (int c = 0; c < 3; ++c) {
+    ft::FMaps m{};
+    const bool ok = fmap(&m.m[0], g, true, uh[c], ft::Halo1<double, SH>::BW, SH) &&
+                    fmap(&m.m[1], g, true, p, ft::Halo1<double, SH>::BW, SH) &&
+                    fmap(&m.m[2], g, true, src[c], ft::Halo1<double, SH>::BW, SH) &&
+                    fmap(&m.m[3], g, sizeof(T) == 8, k + c * f, ft::Halo1<T, SH>::BW, SH);
+    if (!ok) return set_error(NN4_ECUDA, "tensor map encode failed (predictor)");
+    kb<<<gb, dim3(32, TYT), sb, st>>>(m, G, mk, vf, zc2, c, fp->dt, (T)fp->dt, C, uh[0], uh[1], uh[2], un[c], ut[c],
+                                      uh_next ? uh_next[c] : nullptr);
+  }
   return check_cuda(cudaGetLastError(), "momentum predictor");
 }
 

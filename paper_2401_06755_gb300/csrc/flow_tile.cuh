@@ -11,8 +11,11 @@
 // State is FP64 in memory; the arithmetic runs in T (double, or float for the FP32-compute form).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "common.cuh"
 
 namespace nn4 {
 namespace ft {
@@ -76,9 +79,11 @@ __device__ __forceinline__ T dot3(const W3<T>& a, T v0, T v1, T v2) {
   return fma(a.w[0], v0, fma(a.w[1], v1, a.w[2] * v2));
 }
 
-// ---------------------------------------------------------------- FP64 <-> FP32 on the integer pipe
+// ---------------------------------------------------------------- FP64 <-> FP32 conversions
 // The FP64 pipe of this part is narrow (about 2 operations per clock per SM), and a hardware
-// conversion between FP64 and FP32 issues on it.  These conversions use integer instructions.
+// conversion between FP64 and FP32 issues on it.  Kernels bound by instruction issue use the
+// hardware conversion (one instruction on an otherwise idle pipe); kernels bound by memory that
+// convert every staged value use these integer-pipe conversions instead (conv_int).
 // to_f32: IEEE round to nearest even; results below the FP32 normal range flush to signed zero,
 // results beyond it become infinity; NaN stays NaN.
 __device__ __forceinline__ float f64_to_f32(double x) {
@@ -134,14 +139,30 @@ __device__ __forceinline__ double from64<double>(double v) {
 }
 template <>
 __device__ __forceinline__ float from64<float>(double v) {
-  return f64_to_f32(v);
+  return __double2float_rn(v);
 }
 __device__ __forceinline__ double to64(double v) { return v; }
-__device__ __forceinline__ double to64(float v) { return f32_to_f64(v); }
+__device__ __forceinline__ double to64(float v) { return (double)v; }
 
 template <typename T>
 __device__ __forceinline__ T conv(double v) {
   return from64<T>(v);
+}
+// conversion on the integer pipe (for kernels bound by memory, where the FP64 pipe that carries
+// the hardware conversion would become the limit)
+template <typename T>
+__device__ __forceinline__ T conv_int(double v);
+template <>
+__device__ __forceinline__ double conv_int<double>(double v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ float conv_int<float>(double v) {
+  return f64_to_f32(v);
+}
+template <typename T>
+__device__ __forceinline__ T conv_int(float v) {
+  return (T)v;
 }
 template <typename T>
 __device__ __forceinline__ T conv(float v);
@@ -161,55 +182,8 @@ __device__ __forceinline__ T load_as(const float* p) {
 
 // store a computed value in the precision of the array
 __device__ __forceinline__ void store_as(double* p, double v) { *p = v; }
-__device__ __forceinline__ void store_as(double* p, float v) { *p = f32_to_f64(v); }
+__device__ __forceinline__ void store_as(double* p, float v) { *p = to64(v); }
 __device__ __forceinline__ void store_as(float* p, float v) { *p = v; }
-
-// ---------------------------------------------------------------- plane staging
-// A staged plane holds the region x in [xs, xs + SW), y in [ys, ys + SH) of one z-plane, as T,
-// row stride SW.  Indices outside the grid are clamped into it: every filter weight that reaches
-// them is zero, so any finite value does.  Stage<R, SW, SH, NT>: the loads of one plane are issued
-// into registers (issue) one step before they are written to shared memory (commit), so their
-// latency overlaps the arithmetic of the previous plane.  R: the element type in memory.
-template <typename R, int SW, int SH, int NT>
-struct Stage {
-  static constexpr int N = SW * SH;
-  static constexpr int E = (N + NT - 1) / NT;
-  R reg[E];
-
-  template <typename T>
-  __device__ __forceinline__ void issue(const R* __restrict__ src, const Geo<T>& g, int xs, int ys, int z, int tid) {
-    const int zc = min(max(z, 0), g.nz - 1);
-    const R* base = src + (long long)zc * g.plane;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int idx = tid + e * NT;
-      if (idx < N) {
-        const int r = idx / SW, c = idx - r * SW;
-        const int gx = min(max(xs + c, 0), g.nx - 1), gy = min(max(ys + r, 0), g.ny - 1);
-        reg[e] = __ldg(base + (long long)gy * g.pitch + gx);
-      }
-    }
-  }
-
-  template <typename T>
-  __device__ __forceinline__ void commit(T* dst, int tid) const {
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int idx = tid + e * NT;
-      if (idx < N) dst[idx] = conv<T>(reg[e]);
-    }
-  }
-
-  // commit a + b * value (the density rho = rho_g + (rho_l - rho_g) C formed at staging)
-  template <typename T>
-  __device__ __forceinline__ void commit_affine(T* dst, int tid, T a, T b) const {
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int idx = tid + e * NT;
-      if (idx < N) dst[idx] = fma(b, conv<T>(reg[e]), a);
-    }
-  }
-};
 
 // The 3 x (RY + 2) values around a thread's column of RY nodes: v[rr][c] = plane value at row
 // r0 + rr, column c0 + c of the staged region (row stride SW).
@@ -260,6 +234,88 @@ __device__ __forceinline__ void zshift(T (&acc)[3]) {
   acc[1] = acc[2];
   acc[2] = T(0);
 }
+
+}  // namespace ft
+}  // namespace nn4
+
+namespace nn4 {
+namespace ft {
+
+// ---------------------------------------------------------------- TMA plane ring
+// The staged planes of the flow kernels arrive by 3D TMA tile loads (cp.async.bulk.tensor) into a
+// ring of NS raw slots in dynamic shared memory, NS - 1 planes ahead of the plane being computed;
+// all boxes of one plane complete on that slot's mbarrier.  A box starts at an x coordinate
+// rounded down to 16 bytes (CO elements before the first column the kernel needs) and is
+// zero-filled outside the grid (every filter weight that reaches those nodes is zero).  After its
+// barrier completes, a plane is converted once into the compute type (a compute slot of
+// SW x SH values, row stride SW), which the x-y filters then read.
+template <typename R, int BW_, int CO_, int BH_>
+struct Box {
+  using type = R;
+  static constexpr int BW = BW_, CO = CO_, BH = BH_;
+  static constexpr int TX = BW_ * BH_ * (int)sizeof(R);   // bytes the TMA load delivers
+  static constexpr int BYTES = (TX + 127) / 128 * 128;     // its footprint in a slot
+};
+
+// Box of a field with a one-node halo around a 32-wide tile that starts at a multiple of 32:
+// FP64 starts 2 columns early (16 bytes), FP32 4.
+template <typename R, int SH>
+using Halo1 = Box<R, sizeof(R) == 8 ? 36 : 40, sizeof(R) == 8 ? 1 : 3, SH>;
+// Box of an FP64 field with a two-node halo around a 30-wide tile that starts at a multiple of
+// 30 (the two-stage kernels): the first column needed is already 16-byte aligned.
+template <int SH>
+using Halo2 = Box<double, 34, 0, SH>;
+
+// raw box (row stride BW, first needed column CO) -> compute slot (SW x SH, type T); IC: convert
+// on the integer pipe
+template <typename B, int SW, int SH, int NT, bool IC = false, typename T>
+__device__ __forceinline__ void convert_box(T* __restrict__ dst, const unsigned char* __restrict__ raw, int tid) {
+  const typename B::type* src = reinterpret_cast<const typename B::type*>(raw);
+  for (int e = tid; e < SW * SH; e += NT) {
+    const int r = e / SW, c = e - r * SW;
+    const typename B::type v = src[r * B::BW + c + B::CO];
+    dst[e] = IC ? conv_int<T>(v) : conv<T>(v);
+  }
+}
+
+// the same, storing a + b * value (the density from C)
+template <typename B, int SW, int SH, int NT, bool IC = false, typename T>
+__device__ __forceinline__ void convert_box_affine(T* __restrict__ dst, const unsigned char* __restrict__ raw, int tid,
+                                                   T a, T b) {
+  const typename B::type* src = reinterpret_cast<const typename B::type*>(raw);
+  for (int e = tid; e < SW * SH; e += NT) {
+    const int r = e / SW, c = e - r * SW;
+    const typename B::type v = src[r * B::BW + c + B::CO];
+    dst[e] = fma(b, IC ? conv_int<T>(v) : conv<T>(v), a);
+  }
+}
+
+// Plane bookkeeping of a block that stages planes j0, j0 + 1, ...: slot and barrier phase.
+template <int NS>
+struct Ring {
+  uint64_t* bar;
+  unsigned char* raw;
+  int slot_bytes, j0;
+  __device__ __forceinline__ int slot(int z) const { return (z - j0) % NS; }
+  __device__ __forceinline__ uint32_t parity(int z) const { return (uint32_t)(((z - j0) / NS) & 1); }
+  __device__ __forceinline__ unsigned char* at(int z) const { return raw + (size_t)slot(z) * slot_bytes; }
+  __device__ __forceinline__ uint64_t* barrier(int z) const { return &bar[slot(z)]; }
+  __device__ __forceinline__ bool wait(int z) const { return mbar_wait_bounded(barrier(z), parity(z)); }
+  // thread 0: initialise the barriers (then the caller synchronises)
+  __device__ __forceinline__ void init() const {
+    for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+    fence_barrier_init();
+  }
+  // after a failed wait: wait (bounded) for every plane issued and not yet consumed
+  __device__ __forceinline__ void drain(int first_unconsumed, int last_issued) const {
+    for (int z = first_unconsumed; z <= last_issued; ++z) mbar_wait_bounded(barrier(z), parity(z));
+  }
+};
+
+// Up to four tensor maps of one kernel launch (64-byte aligned, passed as a grid constant).
+struct alignas(64) FMaps {
+  CUtensorMap m[4];
+};
 
 }  // namespace ft
 }  // namespace nn4
