@@ -718,10 +718,23 @@ def run_batched(nn4, torch, inner, cycles, steps, warmup, rtol=RTOL):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     lat = sorted(lat)
+    tuned = batch.query()
+    s_bytes = {nn4.F64: 8, nn4.F32: 4, nn4.BF16: 2}[inner]
+    hbm = _load_peaks()["hbm_gbs"]
+    roof = []
+    for e in tuned:  # the batched Jacobi launch per level step: x (haloed), b read, e written
+        if e["jacobi_us"] > 0 and e["nodes"] > 0:
+            gbs = 3 * s_bytes * e["nodes"] / (e["jacobi_us"] * 1e-6) / 1e9
+            roof.append({"kernel": f"batch:jacobi:L{e['level']}", "bound": "hbm", "achieved": gbs, "peak": hbm,
+                         "unit": "GB/s", "frac": gbs / hbm, "avg_us": e["jacobi_us"],
+                         "algorithmic": f"{3 * s_bytes} B x {e['nodes']} nodes (x, b in; e out)",
+                         "shape": e["shape"], "zmax": e["zmax"]})
     return {"inner": {nn4.F64: "f64", nn4.F32: "f32", nn4.BF16: "bf16"}[inner], "inner_cycles": cycles,
             "solves_per_s": 96 * 1000.0 / ms, "ms_per_batch": ms, "p50_ms": lat[len(lat) // 2],
             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "iterations_median": statistics.median(its),
-            "instances": 96, "nodes": int(sum(G.n[0] ** 3 for G in grids)), "status": code}
+            "instances": 96, "nodes": int(sum(G.n[0] ** 3 for G in grids)), "status": code,
+            "tuned_shapes": [{k: e[k] for k in ("level", "shape", "zmax", "jacobi_us", "items")} for e in tuned],
+            "roofline_kernels": roof}
 
 
 BUBBLE_RATIO_NOTE = (

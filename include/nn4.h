@@ -235,11 +235,30 @@ typedef struct nn4_batch_s* nn4_batch;
  * `inner_cycles` V-cycles per outer FP64 defect-correction iteration (Section 2.4's repeated
  * cycles); `check_every` sets how often the host reads the per-instance convergence flags.  Every
  * step of the cycle is one launch over the work items of all instances (the batching form; not
- * in the paper).  Allocates all workspace here.  Errors: NN4_EINVAL, NN4_EUNSUPPORTED (unequal
+ * in the paper).  With `autotune` (default on) the Jacobi launch of every level step is timed here
+ * for each compiled tile shape and z-march depth cap and the fastest kept (nn4_batch_query);
+ * `pass_shape` in 0 .. 3 forces one shape.  Allocates all workspace here.  Errors: NN4_EINVAL, NN4_EUNSUPPORTED (unequal
  * spacings, fewer than two levels, coarsest level above 1024 free nodes), NN4_ENOMEM. */
 int nn4_batch_create(const nn4_grid* grids, int32_t count, const nn4_plan_opts* opts, nn4_batch* out);
 
 int nn4_batch_destroy(nn4_batch b);
+
+/* What the batch's autotuner chose for the Jacobi launch of each level step (level 0 = the finest
+ * level of every instance; levels that join the one-CTA coarse tails have no such launch).  Not in
+ * the paper: tile shapes and z-march depths are implementation choices.  shape: index of the
+ * compiled tile shape (0 .. 3, the first four of nn4_pass_shapes()); zmax: the cap on output planes
+ * per work item; jacobi_us: the launch's measured time at creation (0 when not timed: a forced or
+ * default shape); items: work items of the launch; nodes: nodes it covers over all instances. */
+typedef struct {
+  int32_t levels;
+  int32_t shape[16];
+  int32_t zmax[16];
+  float jacobi_us[16];
+  int32_t items[16];
+  int64_t nodes[16];
+} nn4_batch_info;
+
+int nn4_batch_query(nn4_batch b, nn4_batch_info* info);
 
 /* Solves every instance from its x (bs[i], xs[i]: host arrays of device pointers to FP64 arrays)
  * until its own relative residual <= rtol or max_iters outer iterations; converged instances stop

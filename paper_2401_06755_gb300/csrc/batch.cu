@@ -143,6 +143,10 @@ struct BatchImpl {
     int count = 0, total = 0;
   };
   std::vector<PassSet> jac;       // Jacobi at slot l (l < tail_start of the instance)
+  std::vector<PassCfg> jac_cfg;   // tile shape of slot l's Jacobi launch (autotuned)
+  std::vector<int> jac_shape, jac_zmax;
+  std::vector<float> jac_us;      // its measured time at creation (0: not timed)
+  PassCfg res_cfg;                // tile shape of the FP64 outer residual
   PassSet rr0;                    // level-0 residual + restriction (inner, cycles >= 2)
   PassSet res64;                  // FP64 outer residual
   struct XferSet {
@@ -273,7 +277,8 @@ int upload(BatchImpl* B, std::vector<E>& v, E** d) {
 }
 
 int make_pass(BatchImpl* B, std::vector<BatchPass>& v, nn4_dtype dt, int inst, const LevelGeom& g, const Coef8& L,
-              const void* x, const void* b, void* out, double omega, double* norm2, int* total) {
+              const void* x, const void* b, void* out, double omega, double* norm2, int* total, const PassCfg& shape,
+              int zmax) {
   BatchPass bp;
   std::memset(&bp, 0, sizeof(bp));
   bp.args.g = g;
@@ -282,19 +287,20 @@ int make_pass(BatchImpl* B, std::vector<BatchPass>& v, nn4_dtype dt, int inst, c
   bp.args.b = b;
   bp.args.out = out;
   bp.args.norm2 = norm2;
-  const PassCfg cfg = batch_pass_cfg(dt);
-  PassCfg c = cfg;
-  // a few output planes per item keep the items many and short (latency across instances)
+  PassCfg c = shape;
+  // a few output planes per item keep the items many and short (latency across instances); zmax
+  // caps the z-march depth
   int zc = g.nz;
-  const int tiles = ((g.nx + 31) / 32) * ((g.ny + 15) / 16);
+  const int tx = 32 * shape.wx, ty = shape.tyt * shape.ry;
+  const int tiles = ((g.nx + tx - 1) / tx) * ((g.ny + ty - 1) / ty);
   while (zc > 8 && tiles * ((g.nz + zc - 1) / zc) < 64) zc = (zc + 1) / 2;
-  if (zc > 32) zc = 32;
+  if (zc > zmax) zc = zmax;
   bp.args.zchunk = zc;
   c.zchunk = zc;
   if (!make_pass_maps(&bp.maps, dt, bp.args, c, x, nullptr)) return set_error(NN4_ECUDA, "tensor map encode failed");
   bp.inst = inst;
   bp.first = *total;
-  *total += batch_pass_tiles(dt, &bp);
+  *total += batch_pass_tiles(dt, &bp, c);
   v.push_back(bp);
   return NN4_OK;
 }
@@ -337,6 +343,80 @@ void make_xfer(std::vector<BatchXfer>& v, int inst, bool prolong, const LevelGeo
   v.push_back(X);
 }
 
+// ---------------------------------------------------------------- autotuner of the batched passes
+// The Jacobi launch of level slot l (every instance that has that level in one launch) is timed
+// at creation for each compiled tile shape and z-march depth cap, on the batch's own (zeroed)
+// arrays with every instance active, and the fastest is kept.  plan option pass_shape >= 0 forces
+// a shape (the cap stays at 32); autotune = 0 keeps shape 0 with the cap 32.
+int build_jacobi(BatchImpl* B, int l, const PassCfg& shape, int zmax, std::vector<BatchPass>& v, int* total) {
+  v.clear();
+  *total = 0;
+  int rc;
+  for (int i = 0; i < B->count; ++i) {
+    BInst& I = B->inst[i];
+    if (l >= I.tail_start) continue;
+    BLevel& L = I.lv[l];
+    if ((rc = make_pass(B, v, B->T, i, L.g, L.L, L.t, L.r, L.e, B->o.omega, nullptr, total, shape, zmax))) return rc;
+  }
+  return NN4_OK;
+}
+
+int tune_jacobi(BatchImpl* B, int l, std::vector<BatchPass>& v, int* total) {
+  B->jac_cfg.resize(B->maxlev, batch_pass_cfg(B->T));
+  B->jac_shape.resize(B->maxlev, 0);
+  B->jac_zmax.resize(B->maxlev, 32);
+  B->jac_us.resize(B->maxlev, 0.0f);
+  std::vector<std::pair<int, int>> cands;  // (shape, z cap)
+  const int forced = B->o.pass_shape;
+  if (forced >= 0 && forced < num_batch_shapes())
+    cands.push_back({forced, 32});
+  else if (B->o.autotune)
+    for (int sh = 0; sh < num_batch_shapes(); ++sh)
+      for (int zm : {16, 32, 64}) cands.push_back({sh, zm});
+  else
+    cands.push_back({0, 32});
+  int rc;
+  int best = 0;
+  float best_us = 0.0f;
+  if (cands.size() > 1) {
+    cudaEvent_t e0, e1;
+    if ((rc = check_cuda(cudaEventCreate(&e0), "event")) || (rc = check_cuda(cudaEventCreate(&e1), "event"))) return rc;
+    for (size_t c = 0; c < cands.size(); ++c) {
+      const PassCfg sh = batch_shape_cfg(cands[c].first);
+      int tot = 0;
+      if ((rc = build_jacobi(B, l, sh, cands[c].second, v, &tot))) break;
+      if (v.empty()) break;
+      BatchPass* d = nullptr;
+      if ((rc = check_cuda(cudaMalloc(&d, sizeof(BatchPass) * v.size()), "tuning table"))) break;
+      rc = check_cuda(cudaMemcpy(d, v.data(), sizeof(BatchPass) * v.size(), cudaMemcpyHostToDevice), "tuning table");
+      const int reps = 5;
+      float ms = 0.0f;
+      for (int r = 0; !rc && r < 2; ++r) rc = launch_pass_batch(B->T, OP_JACOBI, sh, d, (int)v.size(), tot, nullptr, 0);
+      if (!rc) rc = check_cuda(cudaEventRecord(e0, 0), "event");
+      for (int r = 0; !rc && r < reps; ++r) rc = launch_pass_batch(B->T, OP_JACOBI, sh, d, (int)v.size(), tot, nullptr, 0);
+      if (!rc) rc = check_cuda(cudaEventRecord(e1, 0), "event");
+      if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "event");
+      if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event");
+      cudaFree(d);
+      if (rc) break;
+      const float us = 1e3f * ms / reps;
+      if (c == 0 || us < best_us) {
+        best = (int)c;
+        best_us = us;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+  }
+  const PassCfg sh = batch_shape_cfg(cands[best].first);
+  B->jac_cfg[l] = sh;
+  B->jac_shape[l] = cands[best].first;
+  B->jac_zmax[l] = cands[best].second;
+  B->jac_us[l] = best_us;
+  return build_jacobi(B, l, sh, cands[best].second, v, total);
+}
+
 // ---------------------------------------------------------------- the batched cycle
 int bcycle(BatchImpl* B, bool first, cudaStream_t s, int64_t* kernels) {
   const nn4_dtype T = B->T;
@@ -359,12 +439,16 @@ int bcycle(BatchImpl* B, bool first, cudaStream_t s, int64_t* kernels) {
   for (int l = (int)B->jac.size() - 1; l >= 1; --l) {
     if (B->jac[l].count == 0) continue;
     if ((rc = launch_xfer_batch(T, true, B->prol[l].d, B->prol[l].count, B->prol[l].total, B->active, s))) return rc;
-    if ((rc = launch_pass_batch(T, OP_JACOBI, B->jac[l].d, B->jac[l].count, B->jac[l].total, B->active, s))) return rc;
+    if ((rc = launch_pass_batch(T, OP_JACOBI, B->jac_cfg[l], B->jac[l].d, B->jac[l].count, B->jac[l].total, B->active,
+                                s)))
+      return rc;
     *kernels += 2;
   }
   const auto& p0 = first ? B->prol[0] : B->prol0_base;
   if ((rc = launch_xfer_batch(T, true, p0.d, p0.count, p0.total, B->active, s))) return rc;
-  if ((rc = launch_pass_batch(T, OP_JACOBI, B->jac[0].d, B->jac[0].count, B->jac[0].total, B->active, s))) return rc;
+  if ((rc = launch_pass_batch(T, OP_JACOBI, B->jac_cfg[0], B->jac[0].d, B->jac[0].count, B->jac[0].total, B->active,
+                              s)))
+    return rc;
   *kernels += 2;
   return NN4_OK;
 }
@@ -373,7 +457,7 @@ int outer_residual_batch(BatchImpl* B, cudaStream_t s, int64_t* kernels) {
   int rc;
   if ((rc = check_cuda(cudaMemsetAsync(B->rn, 0, sizeof(double) * B->count, s), "zero norms"))) return rc;
   *kernels += 1;
-  return launch_pass_batch(NN4_F64, OP_RESIDUAL, B->res64.d, B->res64.count, B->res64.total, B->active, s);
+  return launch_pass_batch(NN4_F64, OP_RESIDUAL, B->res_cfg, B->res64.d, B->res64.count, B->res64.total, B->active, s);
 }
 
 int biteration(BatchImpl* B, cudaStream_t s, int64_t* kernels) {
@@ -503,6 +587,7 @@ int nn4_batch_create(const nn4_grid* grids, int32_t count, const nn4_plan_opts* 
   std::vector<BatchXfer> prol0b;
   std::vector<TailArgs> tails(count);
   std::vector<BOuter> outer(count);
+  B->res_cfg = batch_pass_cfg(NN4_F64);
   B->jac.resize(B->maxlev);
   B->restr.resize(B->maxlev);
   B->prol.resize(B->maxlev);
@@ -514,14 +599,14 @@ int nn4_batch_create(const nn4_grid* grids, int32_t count, const nn4_plan_opts* 
     const int ts = I.tail_start;
     for (int l = 0; l < ts; ++l) {
       BLevel& L = I.lv[l];
-      if ((rc = make_pass(B, jac[l], T, i, L.g, L.L, L.t, L.r, L.e, o.omega, nullptr, &tot_jac[l]))) return fail(rc);
       make_xfer(restr[l], i, false, L.g, I.lv[l + 1].g, l == 0 ? L.r : L.r, I.lv[l + 1].r, nullptr, &tot_restr[l]);
       make_xfer(prol[l], i, true, L.g, I.lv[l + 1].g, I.lv[l + 1].e, L.t, nullptr, &tot_prol[l]);
     }
     BLevel& L0 = I.lv[0];
     if ((rc = make_rr_pass(rr0, T, i, L0.g, L0.L, I.lv[1].g, L0.e, L0.r, I.lv[1].r, &tot_rr0))) return fail(rc);
     make_xfer(prol0b, i, true, L0.g, I.lv[1].g, I.lv[1].e, L0.t, L0.e, &tot_p0b);
-    if ((rc = make_pass(B, res64, NN4_F64, i, I.g64, I.L64, I.x64, I.b64, I.r64, o.omega, B->rn + i, &tot_res64)))
+    if ((rc = make_pass(B, res64, NN4_F64, i, I.g64, I.L64, I.x64, I.b64, I.r64, o.omega, B->rn + i, &tot_res64,
+                        B->res_cfg, 32)))
       return fail(rc);
     TailArgs& ta = tails[i];
     std::memset(&ta, 0, sizeof(ta));
@@ -551,6 +636,7 @@ int nn4_batch_create(const nn4_grid* grids, int32_t count, const nn4_plan_opts* 
     rowblocks += (int)(((long long)I.g64.ny * I.g64.nz + 7) / 8);
   }
   for (int l = 0; l < B->maxlev; ++l) {
+    if ((rc = tune_jacobi(B, l, jac[l], &tot_jac[l]))) return fail(rc);
     if ((rc = upload(B, jac[l], &B->jac[l].d)) || (rc = upload(B, restr[l], &B->restr[l].d)) ||
         (rc = upload(B, prol[l], &B->prol[l].d)))
       return fail(rc);
@@ -576,6 +662,24 @@ int nn4_batch_create(const nn4_grid* grids, int32_t count, const nn4_plan_opts* 
   nn4_batch h = new nn4_batch_s;
   h->impl = B;
   *out = h;
+  return NN4_OK;
+}
+
+int nn4_batch_query(nn4_batch b, nn4_batch_info* info) {
+  if (!b || !info) return set_error(NN4_EINVAL, "NULL argument");
+  BatchImpl* B = b->impl;
+  std::memset(info, 0, sizeof(*info));
+  info->levels = std::min<int>((int)B->jac.size(), 16);
+  for (int l = 0; l < info->levels; ++l) {
+    info->shape[l] = l < (int)B->jac_shape.size() ? B->jac_shape[l] : 0;
+    info->zmax[l] = l < (int)B->jac_zmax.size() ? B->jac_zmax[l] : 32;
+    info->jacobi_us[l] = l < (int)B->jac_us.size() ? B->jac_us[l] : 0.0f;
+    info->items[l] = B->jac[l].total;
+    long long nodes = 0;
+    for (const auto& I : B->inst)
+      if (l < I.tail_start) nodes += (long long)I.lv[l].g.nx * I.lv[l].g.ny * I.lv[l].g.nz;
+    info->nodes[l] = nodes;
+  }
   return NN4_OK;
 }
 

@@ -101,13 +101,16 @@ struct alignas(64) BatchPass {
   int tiles_x, tiles_y;
 };
 
-// Batched stencil pass over `count` instances (constant coefficient, default tile shape); `items`
-// is a device array; `active` (device, nullable) skips converged instances.
-int launch_pass_batch(nn4_dtype dt, int op, const BatchPass* items, int count, int total, const int* active,
-                      cudaStream_t s);
-// Fills the tiling fields of a batch entry for the default tile shape (returns its item count).
-int batch_pass_tiles(nn4_dtype dt, BatchPass* bp);
+// Batched stencil pass over `count` instances (constant coefficient) with tile shape `cfg` (one of
+// the num_batch_shapes() shapes; every entry of `items` was built for it); `items` is a device
+// array; `active` (device, nullable) skips converged instances.
+int launch_pass_batch(nn4_dtype dt, int op, const PassCfg& cfg, const BatchPass* items, int count, int total,
+                      const int* active, cudaStream_t s);
+// Fills the tiling fields of a batch entry for tile shape cfg (returns its item count).
+int batch_pass_tiles(nn4_dtype dt, BatchPass* bp, const PassCfg& cfg);
 PassCfg batch_pass_cfg(nn4_dtype dt);
+int num_batch_shapes();
+PassCfg batch_shape_cfg(int index);
 
 // stencil.cu: constant coefficient (k == nullptr) or Eq. k-T (k given).  Every input is read with
 // TMA; the maps are built here unless `maps` is given (built with make_pass_maps for this cfg).

@@ -74,51 +74,76 @@ int dispatch_op(int op, int vc, const PassArgs& a, const PassCfg& cfg, const Map
   return set_error(NN4_EINVAL, "bad stencil op");
 }
 
-template <typename T, int OP, bool ISO>
+template <typename T, int OP, bool ISO, int WX, int RY, int TYT, int S>
 int launch_batch_t(const BatchPass* items, int count, int total, const int* active, cudaStream_t st) {
-  using Lay = PassLayout<T, OP, 0, ISO, 1, 4, 4, 3>;
-  auto kern = k_pass_batch<T, OP, 0, ISO, 1, 4, 4, 3>;
+  using Lay = PassLayout<T, OP, 0, ISO, WX, RY, TYT, S>;
+  auto kern = k_pass_batch<T, OP, 0, ISO, WX, RY, TYT, S>;
   const size_t smem = Lay::SMEM;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(batched pass)");
   }
-  const int grid = std::min(total, 152 * 8);
-  kern<<<grid, dim3(32, 4), smem, st>>>(items, count, total, active);
+  // persistent CTAs: as many as are resident at once, striding over the items
+  const int grid = (int)resident_grid((const void*)kern, 32 * WX * TYT, smem, total);
+  kern<<<grid, dim3(32 * WX, TYT), smem, st>>>(items, count, total, active);
   return check_cuda(cudaGetLastError(), "batched stencil pass launch");
+}
+
+// the batched passes compile the first four tile shapes of kCfgs for every storage type
+constexpr int kBatchShapes = 4;
+
+template <typename T, int OP>
+int launch_batch_shape(const PassCfg& c, const BatchPass* items, int count, int total, const int* active,
+                       cudaStream_t st) {
+  for (int i = 0; i < kBatchShapes; ++i)
+    if (c.wx == kCfgs[i][0] && c.ry == kCfgs[i][1] && c.tyt == kCfgs[i][2] && c.stages == kCfgs[i][3]) {
+      switch (i) {
+        case 0: return launch_batch_t<T, OP, true, 1, 4, 4, 3>(items, count, total, active, st);
+        case 1: return launch_batch_t<T, OP, true, 2, 2, 4, 4>(items, count, total, active, st);
+        case 2: return launch_batch_t<T, OP, true, 1, 2, 8, 3>(items, count, total, active, st);
+        case 3: return launch_batch_t<T, OP, true, 2, 4, 2, 4>(items, count, total, active, st);
+      }
+    }
+  return set_error(NN4_EINVAL, "unsupported batched tile shape");
 }
 
 }  // namespace
 
-PassCfg batch_pass_cfg(nn4_dtype dt) {
+PassCfg batch_pass_cfg(nn4_dtype dt) { return batch_shape_cfg(0); }
+
+int num_batch_shapes() { return kBatchShapes; }
+
+PassCfg batch_shape_cfg(int index) {
   PassCfg c;
-  c.wx = 1;
-  c.ry = 4;
-  c.tyt = 4;
-  c.stages = 3;
+  const int i = (index >= 0 && index < kBatchShapes) ? index : 0;
+  c.wx = kCfgs[i][0];
+  c.ry = kCfgs[i][1];
+  c.tyt = kCfgs[i][2];
+  c.stages = kCfgs[i][3];
   c.zchunk = 0;
   return c;
 }
 
-int batch_pass_tiles(nn4_dtype, BatchPass* bp) {
+int batch_pass_tiles(nn4_dtype, BatchPass* bp, const PassCfg& cfg) {
   const LevelGeom& g = bp->args.g;
-  bp->tiles_x = (g.nx + 31) / 32;
-  bp->tiles_y = (g.ny + 15) / 16;
+  const int tx = 32 * cfg.wx, ty = cfg.tyt * cfg.ry;
+  bp->tiles_x = (g.nx + tx - 1) / tx;
+  bp->tiles_y = (g.ny + ty - 1) / ty;
   const int tz = (g.nz + bp->args.zchunk - 1) / bp->args.zchunk;
   return bp->tiles_x * bp->tiles_y * tz;
 }
 
-int launch_pass_batch(nn4_dtype dt, int op, const BatchPass* items, int count, int total, const int* active,
-                      cudaStream_t s) {
+int launch_pass_batch(nn4_dtype dt, int op, const PassCfg& cfg, const BatchPass* items, int count, int total,
+                      const int* active, cudaStream_t s) {
   if (total <= 0) return NN4_OK;
   // every instance of a batch has equal spacing per axis (checked at batch creation)
   switch (dt * 4 + op) {
-    case NN4_F64 * 4 + OP_RESIDUAL: return launch_batch_t<double, OP_RESIDUAL, true>(items, count, total, active, s);
-    case NN4_F64 * 4 + OP_JACOBI: return launch_batch_t<double, OP_JACOBI, true>(items, count, total, active, s);
-    case NN4_F32 * 4 + OP_RESIDUAL: return launch_batch_t<float, OP_RESIDUAL, true>(items, count, total, active, s);
-    case NN4_F32 * 4 + OP_JACOBI: return launch_batch_t<float, OP_JACOBI, true>(items, count, total, active, s);
-    case NN4_BF16 * 4 + OP_RESIDUAL: return launch_batch_t<bf16, OP_RESIDUAL, true>(items, count, total, active, s);
-    case NN4_BF16 * 4 + OP_JACOBI: return launch_batch_t<bf16, OP_JACOBI, true>(items, count, total, active, s);
+    case NN4_F64 * 4 + OP_RESIDUAL: return launch_batch_shape<double, OP_RESIDUAL>(cfg, items, count, total, active, s);
+    case NN4_F64 * 4 + OP_JACOBI: return launch_batch_shape<double, OP_JACOBI>(cfg, items, count, total, active, s);
+    case NN4_F32 * 4 + OP_RESIDUAL: return launch_batch_shape<float, OP_RESIDUAL>(cfg, items, count, total, active, s);
+    case NN4_F32 * 4 + OP_JACOBI: return launch_batch_shape<float, OP_JACOBI>(cfg, items, count, total, active, s);
+    case NN4_BF16 * 4 + OP_RESIDUAL: return launch_batch_shape<bf16, OP_RESIDUAL>(cfg, items, count, total, active, s);
+    case NN4_BF16 * 4 + OP_JACOBI: return launch_batch_shape<bf16, OP_JACOBI>(cfg, items, count, total, active, s);
   }
   return set_error(NN4_EINVAL, "unsupported batched pass");
 }

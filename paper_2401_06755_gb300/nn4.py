@@ -72,6 +72,11 @@ class _FlowStats(ctypes.Structure):
                 ("nh_rel", ctypes.c_double)]
 
 
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("shape", ctypes.c_int32 * 16), ("zmax", ctypes.c_int32 * 16),
+                ("jacobi_us", ctypes.c_float * 16), ("items", ctypes.c_int32 * 16), ("nodes", ctypes.c_int64 * 16)]
+
+
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -116,6 +121,7 @@ def lib():
             "nn4_mass_sum": (ctypes.c_int, [G, vp, vp, vp]),
             "nn4_batch_create": (ctypes.c_int, [G, i32, ctypes.POINTER(_PlanOpts), ctypes.POINTER(vp)]),
             "nn4_batch_destroy": (ctypes.c_int, [vp]),
+            "nn4_batch_query": (ctypes.c_int, [vp, ctypes.POINTER(_BatchInfo)]),
             "nn4_pressure_solve_batched": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dbl, i32,
                                                           ctypes.POINTER(_SolveInfo), ctypes.POINTER(ctypes.c_float),
                                                           vp]),
@@ -390,10 +396,12 @@ class Plan:
 class Batch:
     """Many independent constant-coefficient pressure systems of uneven sizes, solved together."""
 
-    def __init__(self, grids, inner=F32, inner_cycles=2, omega=2.0 / 3.0, check_every=1):
+    def __init__(self, grids, inner=F32, inner_cycles=2, omega=2.0 / 3.0, check_every=1, autotune=True,
+                 pass_shape=-1):
         o = _PlanOpts()
         lib().nn4_plan_opts_default(ctypes.byref(o))
         o.inner, o.inner_cycles, o.omega, o.check_every = int(inner), int(inner_cycles), float(omega), int(check_every)
+        o.autotune, o.pass_shape = int(bool(autotune)), int(pass_shape)
         self.grids = list(grids)
         arr = (_Grid * len(self.grids))(*[g.c(torch.float64) for g in self.grids])
         h = ctypes.c_void_p(0)
@@ -410,6 +418,13 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def query(self):
+        """The autotuner's choice per level step: shape, z cap, measured us, items, nodes."""
+        info = _BatchInfo()
+        _check(lib().nn4_batch_query(self._h, ctypes.byref(info)))
+        return [{"level": l, "shape": info.shape[l], "zmax": info.zmax[l], "jacobi_us": info.jacobi_us[l],
+                 "items": info.items[l], "nodes": info.nodes[l]} for l in range(info.levels)]
 
     def solve(self, bs, xs, rtol=1e-8, max_iters=100, stream=None):
         """bs, xs: lists of FP64 storage tensors.  Returns (status, infos, latency_ms)."""

@@ -74,3 +74,35 @@ def test_batched_mixed_reaches_fp64_solutions(inner, cycles):
     # instances stop independently: their iteration counts differ
     its = [i["iterations"] for i in infos]
     assert max(its) > min(its)
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+def test_batched_forced_tile_shape_matches_oracle_cycles(shape):
+    """Every compiled tile shape of the batched Jacobi launch (forced through pass_shape) gives the
+    oracle's sawtooth cycles to 1e-12 per instance after six FP64 iterations."""
+    need_gpu()
+    nn4, gs, Gs, bs = _setup()
+    batch = nn4.Batch(Gs, inner=nn4.F64, inner_cycles=1, pass_shape=shape)
+    assert all(e["shape"] == shape for e in batch.query())
+    B = [nn4.to_field(b, G) for b, G in zip(bs, Gs)]
+    X = [nn4.field(G) for G in Gs]
+    k = 6
+    batch.solve(B, X, rtol=0.0, max_iters=k)
+    for g, G, b, x in zip(gs, Gs, bs, X):
+        xo, _ = mg.pressure_solve(g, b, fixed_cycles=k)
+        xg = nn4.nodes(x, G).cpu().numpy()
+        assert np.linalg.norm(xg - xo) <= 1e-12 * np.linalg.norm(xo)
+
+
+def test_batched_autotuner_reports_its_choice():
+    """With autotuning on, every level step's Jacobi launch was timed at creation; the choice is a
+    compiled shape and z cap, and level 0 covers the finest nodes of every instance."""
+    need_gpu()
+    nn4, gs, Gs, bs = _setup()
+    batch = nn4.Batch(Gs, inner=nn4.F32, inner_cycles=2)
+    q = batch.query()
+    assert q and q[0]["nodes"] == sum(int(np.prod(G.n)) for G in Gs)
+    for e in q:
+        if e["items"] == 0:
+            continue
+        assert 0 <= e["shape"] < 4 and e["zmax"] in (16, 32, 64) and e["jacobi_us"] > 0.0
