@@ -205,17 +205,20 @@ def ncu_summary(path, write_traffic):
     import collections
     import csv
     import re
-    lines = [ln for ln in open(path) if not ln.startswith("==")]
     launches = collections.OrderedDict()
-    for r in csv.DictReader(lines):
-        key = (r["ID"], r["Kernel Name"], r["Grid Size"])
+    rows = []
+    for fi, one in enumerate(path.split(",")):  # several per-kernel captures may be merged
+        lines = [ln for ln in open(one) if not ln.startswith("==")]
+        rows += [(fi, r) for r in csv.DictReader(lines)]
+    for fi, r in rows:
+        key = (fi, r["ID"], r["Kernel Name"], r["Grid Size"])
         v = float(r["Metric Value"].replace(",", ""))
         unit = r["Metric Unit"]
         scale = {"ns": 1e-3, "usecond": 1.0, "us": 1.0, "ms": 1e3, "byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6,
                  "Gbyte": 1e9}.get(unit, 1.0)
         launches.setdefault(key, {})[r["Metric Name"]] = v * scale
     groups = collections.OrderedDict()
-    for (lid, name, grid), m in launches.items():
+    for (fi, lid, name, grid), m in launches.items():
         base = re.sub(r"\(.*", "", name).replace("void ", "").replace("<unnamed>::", "").replace("unnamed>::", "").replace("nn4::", "")
         g = groups.setdefault((base, grid), {"n": 0, "us": 0.0, "dram": 0.0})
         g["n"] += 1
@@ -272,7 +275,8 @@ def main():
     ap.add_argument("--bubble", action="store_true", help="only the rising-bubble time steps (one JSON line)")
     ap.add_argument("--bubble-n", type=int, default=513, help="nodes per axis for the rising bubble")
     ap.add_argument("--bubble-steps", type=int, default=10, help="time steps of the rising bubble")
-    ap.add_argument("--ncu-summary", metavar="CSV", help="summarise an ncu launch list of the timed region")
+    ap.add_argument("--ncu-summary", metavar="CSV", help="summarise an ncu launch list (or several per-kernel "
+                    "captures, comma-separated)")
     ap.add_argument("--write-traffic", action="store_true", help="with --ncu-summary: write profiles/ncu_traffic.json")
     args = ap.parse_args()
     if args.ncu_summary:

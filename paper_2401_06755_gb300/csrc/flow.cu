@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_coef(const __grid_constant__ f
   if (tid == 0)
     for (int z = ring.j0; z <= min(last, ring.j0 + NS - 2); ++z) issue(z);
   bool failed = !ring.wait(ring.j0);
-  ft::convert_box<BC, SW, SH, NT>(cs, ring.at(ring.j0), tid);
+  ft::convert_box<BC, SW, SH, NT, true>(cs, ring.at(ring.j0), tid);
   if (__syncthreads_or(failed)) {
     if (tid == 0) ring.drain(ring.j0, min(last, ring.j0 + NS - 2));
     return;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_coef(const __grid_constant__ f
 #pragma unroll
       for (int r = 0; r < RY; ++r) {
         if (tin && in[r]) {
-          const T im = T(1) / (FX.lump * ly[r] * lz);
+          const T im = ft::qdiv(T(1), FX.lump * ly[r] * lz);
 #pragma unroll
           for (int d = 0; d < 3; ++d) Cdt[d][r] = gacc[d][r][0] * im;
           gt[r] = Ut[0][r] * Cdt[0][r] + Ut[1][r] * Cdt[1][r] + Ut[2][r] * Cdt[2][r];
@@ -240,18 +240,18 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_coef(const __grid_constant__ f
       for (int r = 0; r < RY; ++r) {
         if (!outp[r]) continue;
         const T m = FX.lump * ly[r] * lz;
-        const T a_C = p.alpha_a * (aacc[r][0] / m - gq[r]);  // Eq. a_psi
+        const T a_C = p.alpha_a * (ft::qdiv(aacc[r][0], m) - gq[r]);  // Eq. a_psi
         const T cx = Cdq[0][r], cy = Cdq[1][r], cz = Cdq[2][r];
         const T ax = fabs(cx), ay = fabs(cy), az = fabs(cz), sabs = ax + ay + az;
         // Eq. efficient-kabs (general spacing)
-        const T k_abs = p.alpha_kabs * fabs(a_C) * (p.h[0] * ax + p.h[1] * ay + p.h[2] * az) /
-                        (p.eps_k + sabs * sabs * p.third);
+        const T k_abs = ft::qdiv(p.alpha_kabs * fabs(a_C) * (p.h[0] * ax + p.h[1] * ay + p.h[2] * az),
+                                 p.eps_k + sabs * sabs * p.third);
         // Eqs. normalisation and negativek
         const T gradsq = cx * cx + cy * cy + cz * cz;
         const T uu = Uq[0][r], vv_ = Uq[1][r], ww = Uq[2][r];
-        const T proj = (uu * cx + vv_ * cy + ww * cz) / (p.eps_x + gradsq);
+        const T proj = ft::qdiv(uu * cx + vv_ * cy + ww * cz, p.eps_x + gradsq);
         const T us = fabs(cx * proj) + fabs(cy * proj) + fabs(cz * proj);
-        const T k_neg = -p.beta * (uu * uu + vv_ * vv_ + ww * ww) / (p.eps_x + gradsq * us * p.third);
+        const T k_neg = ft::qdiv(-p.beta * (uu * uu + vv_ * vv_ + ww * ww), p.eps_x + gradsq * us * p.third);
         // detectors with the override (decided on the FP64 value), weights, combination, clamp
         const bool over = c64[r] > p.detect_hi || c64[r] < p.detect_lo;
         const T S[3] = {over ? T(-1) : SxR[0][r], over ? T(-1) : SyR[0][r], over ? T(-1) : Szq[r]};
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_coef(const __grid_constant__ f
     }
     if (s < last) {
       if (!ring.wait(s + 1)) failed = true;
-      ft::convert_box<BC, SW, SH, NT>(cs + ((s + 1 - ring.j0) & 1) * SH * SW, ring.at(s + 1), tid);
+      ft::convert_box<BC, SW, SH, NT, true>(cs + ((s + 1 - ring.j0) & 1) * SH * SW, ring.at(s + 1), tid);
     }
     if (__syncthreads_or(failed)) {
       if (tid == 0) ring.drain(s + 1, min(last, s + NS - 1));
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(32 * TYT) k_vof_update(const __grid_constant__
   };
   auto convert = [&](int z, T* dst) {
     const unsigned char* src = ring.at(z);
-    ft::convert_box<BC, SW, SH, NT>(dst, src, tid);
+    ft::convert_box<BC, SW, SH, NT, true>(dst, src, tid);
 #pragma unroll
     for (int f = 0; f < 3; ++f) ft::convert_box<BK, SW, SH, NT>(dst + (1 + f) * SH * SW, src + BC::BYTES + f * BK::BYTES, tid);
   };
@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(32 * TYT) k_sources(const __grid_constant__ ft
       for (int r = 0; r < RY; ++r) {
         T n[3] = {T(0), T(0), T(0)};
         if (tin && in[r]) {
-          const T im = T(1) / (FX.lump * ly[r] * lz);
+          const T im = ft::qdiv(T(1), FX.lump * ly[r] * lz);
 #pragma unroll
           for (int d = 0; d < 3; ++d) Cdt[d][r] = gacc[d][r][0] * im;
           const T inv = T(1) / (p.eps_t + sqrt(Cdt[0][r] * Cdt[0][r] + Cdt[1][r] * Cdt[1][r] + Cdt[2][r] * Cdt[2][r]));
@@ -1053,7 +1053,7 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_coef(const __grid_constant__ f
   if (tid == 0)
     for (int z = ring.j0; z <= min(last, ring.j0 + NS - 2); ++z) issue(z);
   bool failed = !ring.wait(ring.j0);
-  ft::convert_box<BC, SW, SH, NT>(cs, ring.at(ring.j0), tid);
+  ft::convert_box<BC, SW, SH, NT, true>(cs, ring.at(ring.j0), tid);
   if (__syncthreads_or(failed)) {
     if (tid == 0) ring.drain(ring.j0, min(last, ring.j0 + NS - 2));
     return;
@@ -1123,7 +1123,7 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_coef(const __grid_constant__ f
 #pragma unroll
       for (int r = 0; r < RY; ++r) {
         if (tin && in[r]) {
-          const T im = T(1) / (FX.lump * ly[r] * lz);
+          const T im = ft::qdiv(T(1), FX.lump * ly[r] * lz);
 #pragma unroll
           for (int d = 0; d < 3; ++d) Pdt[d][r] = gacc[d][r][0] * im;
           gt[r] = Ut[0][r] * Pdt[0][r] + Ut[1][r] * Pdt[1][r] + Ut[2][r] * Pdt[2][r];
@@ -1160,16 +1160,16 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_coef(const __grid_constant__ f
       for (int r = 0; r < RY; ++r) {
         if (!outp[r]) continue;
         const T m = FX.lump * ly[r] * lz;
-        const T a = p.alpha_a * (aacc[r][0] / m - gq[r]);  // Eq. a_psi
+        const T a = p.alpha_a * (ft::qdiv(aacc[r][0], m) - gq[r]);  // Eq. a_psi
         const T px = Pdq[0][r], py = Pdq[1][r], pz = Pdq[2][r];
         const T ax = fabs(px), ay = fabs(py), az = fabs(pz), sab = ax + ay + az;
         const T hsum = p.h[0] * ax + p.h[1] * ay + p.h[2] * az;
-        const T k_abs = p.alpha_kabs * fabs(a) * hsum / (p.eps_k + sab * sab * p.third);  // Eq. efficient-kabs
-        const T h_psi = hsum / (p.eps_k + sab);                                           // Eq. h_Psi
+        const T k_abs = ft::qdiv(p.alpha_kabs * fabs(a) * hsum, p.eps_k + sab * sab * p.third);  // Eq. efficient-kabs
+        const T h_psi = ft::qdiv(hsum, p.eps_k + sab);                                             // Eq. h_Psi
         const T u0 = Uq[0][r], u1 = Uq[1][r], u2 = Uq[2][r];
-        const T k_sq = p.alpha_ksq * a * a * h_psi /
-                       (p.eps_k + (fabs(u0 * px) + fabs(u1 * py) + fabs(u2 * pz)) * (px * px + py * py + pz * pz) *
-                                      p.third);  // Eq. k-square
+        const T k_sq = ft::qdiv(p.alpha_ksq * a * a * h_psi,
+                                p.eps_k + (fabs(u0 * px) + fabs(u1 * py) + fabs(u2 * pz)) *
+                                              (px * px + py * py + pz * pz) * p.third);  // Eq. k-square
         const T kmax = p.h[0] * fabs(u0) + p.h[1] * fabs(u1) + p.h[2] * fabs(u2);  // Eq. max-k
         const T c = ft::from64<T>(c64[r]);
         const T rho = p.rho_g + p.rho_d * c, mu = p.mu_g + p.mu_d * c;
@@ -1188,7 +1188,7 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_coef(const __grid_constant__ f
     }
     if (s < last) {
       if (!ring.wait(s + 1)) failed = true;
-      ft::convert_box<BC, SW, SH, NT>(cs + ((s + 1 - ring.j0) & 1) * SH * SW, ring.at(s + 1), tid);
+      ft::convert_box<BC, SW, SH, NT, true>(cs + ((s + 1 - ring.j0) & 1) * SH * SW, ring.at(s + 1), tid);
     }
     if (__syncthreads_or(failed)) {
       if (tid == 0) ring.drain(s + 1, min(last, s + NS - 1));
@@ -1230,10 +1230,10 @@ __global__ void __launch_bounds__(32 * TYT) k_mom_update(const __grid_constant__
   };
   auto convert = [&](int z, T* dst) {
     const unsigned char* src = ring.at(z);
-    ft::convert_box<BD, SW, SH, NT>(dst, src, tid);                                  // psi
-    ft::convert_box<BK, SW, SH, NT>(dst + SH * SW, src + 3 * BD::BYTES, tid);       // k
-    ft::convert_box<BD, SW, SH, NT>(dst + 2 * SH * SW, src + BD::BYTES, tid);       // p
-    ft::convert_box<BD, SW, SH, NT>(dst + 3 * SH * SW, src + 2 * BD::BYTES, tid);   // s
+    ft::convert_box<BD, SW, SH, NT, true>(dst, src, tid);                                  // psi
+    ft::convert_box<BK, SW, SH, NT>(dst + SH * SW, src + 3 * BD::BYTES, tid);             // k
+    ft::convert_box<BD, SW, SH, NT, true>(dst + 2 * SH * SW, src + BD::BYTES, tid);       // p
+    ft::convert_box<BD, SW, SH, NT, true>(dst + 3 * SH * SW, src + 2 * BD::BYTES, tid);   // s
   };
   if (tid == 0) ring.init();
   __syncthreads();

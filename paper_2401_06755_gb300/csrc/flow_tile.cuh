@@ -74,6 +74,11 @@ __device__ __forceinline__ Fac<T> facz(const Geo<T>& g, int k) {
   return fac<T>(k, g.nz, g.h6[2], g.h3[2], g.h2[2], g.ih[2]);
 }
 
+// a / b: IEEE division in FP64; in the FP32-compute form the fast approximate division (a few
+// ulp), well inside that form's stated error
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+
 template <typename T>
 __device__ __forceinline__ T dot3(const W3<T>& a, T v0, T v1, T v2) {
   return fma(a.w[0], v0, fma(a.w[1], v1, a.w[2] * v2));
