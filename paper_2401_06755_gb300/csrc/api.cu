@@ -110,6 +110,25 @@ bool make_tmap_3d(CUtensorMap* map, nn4_dtype dt, const void* base, int nx, int 
   return r == CUDA_SUCCESS;
 }
 
+bool make_tmap_stack(CUtensorMap* map, nn4_dtype dt, const void* base, int nx, int ny, int nz, int nw,
+                     long long pitch, int box_x, int box_y, int box_w) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  const size_t es = dtype_size(dt);
+  CUtensorMapDataType ty = dt == NN4_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                           : dt == NN4_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nw};
+  cuuint64_t strides[3] = {(cuuint64_t)(pitch * es), (cuuint64_t)(pitch * es * ny),
+                           (cuuint64_t)(pitch * es * ny * nz)};
+  cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, (cuuint32_t)box_w};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(map, ty, 4, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 // ---------------------------------------------------------------- validation
 int validate_grid(const nn4_grid* g, nn4_dtype dt, int min_n) {
   if (!g) return set_error(NN4_EINVAL, "grid is NULL");

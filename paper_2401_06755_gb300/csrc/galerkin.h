@@ -24,7 +24,13 @@ int launch_galerkin_next(nn4_dtype ct, const void* af, const LevelGeom& gf, void
 // Elementwise conversion of a 27-array block from type ct to type dt (same pitch).
 int launch_convert27(nn4_dtype ct, const void* src, nn4_dtype dt, void* dst, const LevelGeom& g, cudaStream_t s);
 
-// Residual / Jacobi passes with a 27-array operator (OP_RESIDUAL, OP_JACOBI).
+// Sets the 13 lower arrays of a 27-array block of type ct (NN4_F64 or NN4_F32) from the upper
+// ones (A[i, i+D] := A[i+D, i]), making the stored operator exactly symmetric.
+int launch_symmetrize27(nn4_dtype ct, void* a27, const LevelGeom& g, cudaStream_t s);
+
+// Residual / Jacobi passes with a symmetric 27-array operator (OP_RESIDUAL, OP_JACOBI); only the
+// upper arrays 13..26 are read.  x and b must be 16-byte aligned with pitch * element size a
+// multiple of 16 bytes (TMA tiles).
 int launch_pass27(nn4_dtype dt, int op, const PassArgs& a, const void* x, const void* a27, cudaStream_t s);
 
 // Builds the coefficient hierarchy of plan P (levels >= 1) and returns the coarsest operator as

@@ -73,6 +73,10 @@ int set_error(int code, const std::string& msg);
 int check_cuda(cudaError_t e, const char* what);
 bool make_tmap_3d(CUtensorMap* map, nn4_dtype dt, const void* base, int nx, int ny, int nz,
                   long long pitch, int box_x, int box_y);
+// A stack of nw fields of one grid, field w starting pitch * ny * nz elements after field w - 1
+// (4D map; box (box_x, box_y, 1, box_w)).
+bool make_tmap_stack(CUtensorMap* map, nn4_dtype dt, const void* base, int nx, int ny, int nz, int nw,
+                     long long pitch, int box_x, int box_y, int box_w);
 size_t dtype_size(nn4_dtype dt);
 // SMs of the current device (cached per device).
 int sm_count();

@@ -233,7 +233,7 @@ int build_galerkin_hierarchy(PlanImpl* P, std::vector<double>& dense) {
       rc = launch_galerkin_from_k(ct, P->k64, P->g64, P->lv[0].h, tmp, L.g, 0);
     else
       rc = launch_galerkin_next(ct, prev, gprev, tmp, L.g, 0);
-    if (rc) return rc;
+    if (rc || (rc = launch_symmetrize27(ct, tmp, L.g, 0))) return rc;
     if (P->T == ct) {
       L.a27 = tmp;
     } else {

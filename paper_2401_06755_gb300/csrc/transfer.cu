@@ -1,5 +1,7 @@
 // Inter-grid transfers of the sawtooth multigrid (Section 2.4): stride-2 restriction R = P^T and
 // trilinear prolongation P between a fine vertex grid and the grid of its even-indexed nodes.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -31,75 +33,107 @@ __device__ __forceinline__ void st2(bf16* p, float a, float b) {
 }
 
 // Restriction r_c(I) = sum_{d in {-1,0,1}^3} prod_d (1/2)^|d| r_f(2I + d) over the fine nodes that
-// exist; zero at coarse Dirichlet nodes.  A thread owns coarse column (I, J) over kRz coarse
-// planes (unrolled, so all its loads are in flight together); lane I loads the fine pair
-// (2I, 2I+1) of each row and the node 2I-1.  Consecutive coarse planes share a fine plane, read
-// once.
-constexpr int kRz = 2;
+// exist; zero at coarse Dirichlet nodes.  A CTA owns 32 coarse columns x TYC coarse rows and marches
+// along z over `kchunk` coarse planes: every fine plane 2K-1 .. 2K+1 of its region (fine columns
+// 2 I0 - 1 .. 2 I0 + 63, rows 2 J0 - 1 .. 2 J0 + 2 TYC - 1) arrives as one TMA box in a ring of S
+// stages, each fine value leaves HBM once per chunk, and fine nodes outside the grid arrive as
+// zeros (their weight).  A thread restricts its coarse node in x and y from the box and folds the
+// z weights (1/2, 1, 1/2) into one running sum.  Rows of 32 m + 1 coarse nodes: the last tile's first
+// lane also computes coarse column 32 m.
+template <typename T, int TYC, int S>
+struct RLay {
+  static constexpr int AL = 16 / (int)sizeof(T);
+  static constexpr int BX = (64 + AL + 2 + AL - 1) / AL * AL;  // fine columns 2 I0 - AL .. 2 I0 + 65 at least
+  static constexpr int BY = 2 * TYC + 1;
+  static constexpr int BYTES = BX * BY * (int)sizeof(T);
+  static constexpr int STAGE = (BYTES + 127) / 128 * 128;
+  static constexpr size_t SMEM = (size_t)S * STAGE + S * 8;
+};
+constexpr int kRTy = 8, kRStages = 6;
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_restrict(const T* __restrict__ rf, T* __restrict__ rc, const LevelGeom gf,
-                                                  const LevelGeom gc) {
+template <typename T, int TYC, int S>
+__global__ void __launch_bounds__(32 * TYC) k_restrict(const __grid_constant__ CUtensorMap fmap, T* __restrict__ rc,
+                                                       const LevelGeom gc, int kchunk) {
   using A = typename Acc<T>::type;
-  const int I = blockIdx.x * 32 + threadIdx.x;
-  const int J = blockIdx.y * 4 + threadIdx.y;
-  if (J >= gc.ny) return;
-  // Neighbours that do not exist (past a boundary node) are read at a clamped position with weight
-  // 0, so no load sits behind a branch.
-  const int i0 = 2 * min(I, gc.nx - 1);
-  const bool has_r = i0 + 1 < gf.nx;
-  const int dl = i0 > 0 ? -1 : 0;
-  const A wl = i0 > 0 ? A(0.5) : A(0), wr = A(0.5);
-  const long long rs = gf.pitch, ps = gf.pitch * (long long)gf.ny;
-  const int j0 = 2 * J;
-  const long long om = J > 0 ? -rs : 0, op = j0 + 1 < gf.ny ? rs : 0;
-  const A wm = J > 0 ? A(0.5) : A(0), wp = j0 + 1 < gf.ny ? A(0.5) : A(0);
-  const int K0 = blockIdx.z * kRz;
-  const T* P0 = rf + i0 + rs * j0 + ps * (2 * K0);  // fine plane 2 K0, row 2 J
-  // Every raw value first (fine planes 2K0-1 .. 2K0+2kRz-1, clamped into the grid with weight 0
-  // outside; rows 2J-1, 2J, 2J+1), then the arithmetic: all 2 (2 kRz + 1) 3 loads in flight.
-  constexpr int NPL = 2 * kRz + 1;
-  A c[NPL][3], r[NPL][3], l[NPL][3], wpl[NPL];
+  using Lay = RLay<T, TYC, S>;
+  constexpr int AL = Lay::AL, BX = Lay::BX;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * Lay::STAGE);
+  const int I0 = blockIdx.x * 32, J0 = blockIdx.y * TYC;
+  const int Ks = blockIdx.z * kchunk, Ke = min(gc.nz, Ks + kchunk);
+  const int f0 = 2 * Ks - 1;             // first fine plane (odd)
+  const int nf = 2 * (Ke - Ks) + 1;      // fine planes 2 Ks - 1 .. 2 Ke - 1
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  if (tid == 0) {
 #pragma unroll
-  for (int q = 0; q < NPL; ++q) {
-    const int k = 2 * K0 - 1 + q;
-    const int kc = min(max(k, 0), gf.nz - 1);
-    wpl[q] = (k >= 0 && k < gf.nz) ? A(1) : A(0);
-    const T* pq = P0 + ps * (kc - 2 * K0);
-    const long long ro[3] = {om, 0, op};
-#pragma unroll
-    for (int w = 0; w < 3; ++w) {
-      ld2(pq + ro[w], c[q][w], r[q][w]);  // r lies past the row end for the last column: not used
-      l[q][w] = to_acc(pq[ro[w] + dl]);
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+    prefetch_tmap(&fmap);
+  }
+  __syncthreads();
+  auto issue = [&](int q) {
+    const int s = q % S;
+    mbar_expect_tx(&bars[s], Lay::BYTES);
+    tma_load_3d(smem + s * Lay::STAGE, &fmap, 2 * I0 - AL, 2 * J0 - 1, f0 + q, &bars[s]);
+  };
+  int issued = min(S, nf);
+  if (tid == 0)
+    for (int q = 0; q < issued; ++q) issue(q);
+  const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+  const bool extra = threadIdx.x == 0 && I0 + 32 == gc.nx - 1;
+  const int cb = (2 * threadIdx.y + 1) * BX + 2 * threadIdx.x + AL;  // fine node (2I, 2J) in a box
+  const bool dxy = (gc.dir[2] && J == 0) || (gc.dir[3] && J == gc.ny - 1);
+  const bool dx = (gc.dir[0] && I == 0) || (gc.dir[1] && I == gc.nx - 1);
+  const bool dx2 = gc.dir[1];  // the extra column is the last one
+  const long long cps = gc.pitch * (long long)gc.ny;
+  T* const out = rc + I + gc.pitch * (long long)J;
+  A acc = A(0), acc2 = A(0);
+  bool failed = false;
+  int q = 0;
+  for (; q < nf; ++q) {
+    const int s = q % S;
+    if (!mbar_wait_bounded(&bars[s], (uint32_t)((q / S) & 1))) failed = true;
+    const T* F = reinterpret_cast<const T*>(smem + s * Lay::STAGE);
+    auto row = [&](int c) { return to_acc(F[c]) + A(0.5) * (to_acc(F[c - 1]) + to_acc(F[c + 1])); };
+    auto xy = [&](int c) { return row(c) + A(0.5) * (row(c - BX) + row(c + BX)); };
+    const A v = xy(cb);
+    const A v2 = extra ? xy(cb + 64) : A(0);
+    if ((f0 + q) & 1) {  // odd fine plane: closes coarse plane (f-1)/2, opens (f+1)/2
+      if (q > 0 && !failed && J < gc.ny) {
+        const int K = (f0 + q - 1) >> 1;
+        const bool dz = dxy || (gc.dir[4] && K == 0) || (gc.dir[5] && K == gc.nz - 1);
+        if (I < gc.nx) out[cps * K] = from_acc<T>((dz || dx) ? A(0) : acc + A(0.5) * v);
+        if (extra) out[cps * K + 32] = from_acc<T>((dz || dx2) ? A(0) : acc2 + A(0.5) * v2);
+      }
+      acc = A(0.5) * v;
+      acc2 = A(0.5) * v2;
+    } else {
+      acc += v;
+      acc2 += v2;
+    }
+    if (__syncthreads_or(failed)) {
+      failed = true;
+      break;
+    }
+    if (q + S < nf) {  // every thread is done with stage s: bring fine plane q + S
+      if (tid == 0) issue(q + S);
+      ++issued;
     }
   }
-  A pl[NPL];
-#pragma unroll
-  for (int q = 0; q < NPL; ++q) {
-    A row[3];
-#pragma unroll
-    for (int w = 0; w < 3; ++w) row[w] = c[q][w] + wl * l[q][w] + (has_r ? wr * r[q][w] : A(0));
-    pl[q] = row[1] + wm * row[0] + wp * row[2];
-  }
-  const bool dxy = (gc.dir[0] && I == 0) || (gc.dir[1] && I == gc.nx - 1) || (gc.dir[2] && J == 0) ||
-                   (gc.dir[3] && J == gc.ny - 1);
-  T* out = rc + I + gc.pitch * ((long long)J + (long long)gc.ny * K0);
-  const long long cps = gc.pitch * (long long)gc.ny;
-#pragma unroll
-  for (int t = 0; t < kRz; ++t) {
-    const int K = K0 + t;
-    if (K >= gc.nz) break;
-    const A v = pl[2 * t + 1] + A(0.5) * (wpl[2 * t] * pl[2 * t] + wpl[2 * t + 2] * pl[2 * t + 2]);
-    const bool dn = dxy || (gc.dir[4] && K == 0) || (gc.dir[5] && K == gc.nz - 1);
-    if (I < gc.nx) out[cps * t] = from_acc<T>(dn ? A(0) : v);
+  if (failed && tid == 0) {
+    for (int p = q; p < issued; ++p) mbar_wait_bounded(&bars[p % S], (uint32_t)((p / S) & 1));
   }
 }
 
 // Prolongation e_f (+)= P e_c: each fine node takes the coarse nodes bracketing it, weight 1 at an
-// even index and 1/2 for each of the two parents at an odd index, per axis.  A thread owns the
-// fine pair (2I, 2I+1) of row j over kPz fine planes: x-even = e_c(I), x-odd = (e_c(I) + e_c(I+1))/2.
-// Dirichlet fine nodes keep base (or 0).
-constexpr int kPz = 8;
+// even index and 1/2 for each of the two parents at an odd index, per axis, applied in the order
+// y, then x, then z.  A thread owns coarse column I and coarse row J: the fine pair (2I, 2I+1) of
+// fine rows 2J and 2J+1, over the fine planes of kPc coarse planes (2 kPc fine planes).  Per coarse
+// plane it loads two values (rows J and J+1 of column I) and takes column I+1 from the next lane,
+// forms the four plane values (row parity x column parity) and stores one fine pair per fine row
+// and plane; odd fine planes average two consecutive plane values.  Dirichlet fine nodes keep base
+// (or 0).
+constexpr int kPc = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ ec, T* ef, const T* base, const LevelGeom gc,
@@ -107,64 +141,84 @@ __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ ec, T* ef
   using A = typename Acc<T>::type;
   const int lane = threadIdx.x;
   const int I = blockIdx.x * 32 + lane;
-  const int j = blockIdx.y * 4 + threadIdx.y;
-  if (j >= gf.ny) return;  // whole warps only
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (J >= gc.ny) return;  // whole warps only (J is uniform across the warp)
   const int Ic = min(I, gc.nx - 1);
-  const bool has_next = Ic + 1 < gc.nx;
-  const int J0 = j >> 1, J1 = J0 + (j & 1);
-  // (x-even, x-odd) values of coarse plane K at fine row j
-  // rows J0 and J1 (= J0 for an even j, weight 1/2 each then): the branch-free sum of both
-  const int In = has_next ? Ic + 1 : Ic;
-  const T* const c0 = ec + gc.pitch * (long long)J0;
-  const long long d1 = gc.pitch * (long long)(J1 - J0), cps = gc.pitch * (long long)gc.ny;
-  auto plane = [&](int K, A& ve, A& vo) {
-    const T* r0 = c0 + cps * K;
-    const T* r1 = r0 + d1;
-    const A a = A(0.5) * (to_acc(r0[Ic]) + to_acc(r1[Ic]));
-    const A an = A(0.5) * (to_acc(r0[In]) + to_acc(r1[In]));
-    ve = a;
-    vo = A(0.5) * (a + an);
-  };
-  const int k0 = blockIdx.z * kPz, k1 = min(gf.nz, k0 + kPz);
-  const int K0 = k0 >> 1;
-  A ce[kPz / 2 + 1], co[kPz / 2 + 1];
-  // coarse planes past the grid are clamped (their values only feed fine planes past the grid,
-  // which are not stored), so all coarse loads are issued without a branch
-#pragma unroll
-  for (int t = 0; t <= kPz / 2; ++t) plane(min(K0 + t, gc.nz - 1), ce[t], co[t]);
-  const int i = 2 * I;
-  const bool ok0 = I < gc.nx, ok1 = i + 1 < gf.nx;
-  const bool dy = (gf.dir[2] && j == 0) || (gf.dir[3] && j == gf.ny - 1);
-  const bool d0x = (gf.dir[0] && i == 0) || (gf.dir[1] && i == gf.nx - 1);
-  const bool d1x = gf.dir[1] && i + 1 == gf.nx - 1;
-  T* const out0 = ef + i + gf.pitch * ((long long)j + (long long)gf.ny * k0);
+  const int Jn = min(J + 1, gc.ny - 1);  // row J+1 (clamped: its values then feed no stored node)
+  const long long cps = gc.pitch * (long long)gc.ny;
+  const T* const r0 = ec + Ic + gc.pitch * (long long)J;
+  const long long d1 = gc.pitch * (long long)(Jn - J);
+  const int K0 = blockIdx.z * kPc;
+  const int i = 2 * I, j = 2 * J;
+  const bool ok0 = I < gc.nx, ok1 = i + 1 < gf.nx;  // fine columns 2I and 2I+1 exist
+  const bool okr = j + 1 < gf.ny;                    // fine row 2J+1 exists
+  const bool dx0 = (gf.dir[0] && i == 0) || (gf.dir[1] && i == gf.nx - 1);
+  const bool dx1 = gf.dir[1] && i + 1 == gf.nx - 1;
+  const bool dy0 = (gf.dir[2] && j == 0) || (gf.dir[3] && j == gf.ny - 1);
+  const bool dy1 = gf.dir[3] && j + 1 == gf.ny - 1;
   const long long fps = gf.pitch * (long long)gf.ny;
+  T* const out0 = ef + i + gf.pitch * (long long)j;
+  // plane values of coarse plane K: [row parity][column parity]
+  auto plane = [&](int K, A v[2][2]) {
+    const T* p = r0 + cps * K;
+    const A c0 = to_acc(p[0]), c1 = to_acc(p[d1]);
+    A n0 = __shfl_down_sync(0xffffffffu, c0, 1), n1 = __shfl_down_sync(0xffffffffu, c1, 1);
+    if (lane == 31 || Ic + 1 >= gc.nx) {  // column I+1 from memory (clamped at the last column)
+      const int o = Ic + 1 < gc.nx ? 1 : 0;
+      n0 = to_acc(p[o]);
+      n1 = to_acc(p[d1 + o]);
+    }
+    v[0][0] = c0;                     // even row, even column
+    v[0][1] = A(0.5) * (c0 + n0);     // even row, odd column
+    const A a = A(0.5) * (c0 + c1);   // odd row: y first
+    const A an = A(0.5) * (n0 + n1);
+    v[1][0] = a;
+    v[1][1] = A(0.5) * (a + an);
+  };
+  // one fine plane k from plane values v: Dirichlet nodes keep base (or 0)
+  auto emit = [&](int k, const A v[2][2]) {
+    if (k >= gf.nz) return;
+    const bool dz = (gf.dir[4] && k == 0) || (gf.dir[5] && k == gf.nz - 1);
 #pragma unroll
-  for (int t = 0; t < kPz; ++t) {
-    const int k = k0 + t;
-    if (k >= k1) break;
-    A v0 = (t & 1) ? A(0.5) * (ce[t >> 1] + ce[(t >> 1) + 1]) : ce[t >> 1];
-    A v1 = (t & 1) ? A(0.5) * (co[t >> 1] + co[(t >> 1) + 1]) : co[t >> 1];
-    const bool dz = dy || (gf.dir[4] && k == 0) || (gf.dir[5] && k == gf.nz - 1);
-    T* out = out0 + fps * t;
-    A b0 = A(0), b1 = A(0);
-    if (base) {
-      const T* bp = base + (out - ef);
-      if (ok1) {
-        ld2(bp, b0, b1);
-      } else if (ok0) {
-        b0 = to_acc(bp[0]);
+    for (int r = 0; r < 2; ++r) {
+      if (r == 1 && !okr) break;
+      T* out = out0 + fps * k + gf.pitch * r;
+      const bool dyr = dz || (r ? dy1 : dy0);
+      A b0 = A(0), b1 = A(0);
+      if (base) {
+        const T* bp = base + (out - ef);
+        if (ok1) ld2(bp, b0, b1);
+        else if (ok0) b0 = to_acc(bp[0]);
       }
+      const A v0 = (dyr || dx0) ? b0 : v[r][0] + b0;
+      const A v1 = (dyr || dx1) ? b1 : v[r][1] + b1;
+      if (ok1) st2(out, v0, v1);
+      else if (ok0) out[0] = from_acc<T>(v0);
     }
-    v0 = (dz || d0x) ? b0 : v0 + b0;
-    v1 = (dz || d1x) ? b1 : v1 + b1;
-    if (ok1) {
-      st2(out, v0, v1);
-    } else if (ok0) {
-      out[0] = from_acc<T>(v0);
-    }
+  };
+  A pv[2][2], cv[2][2];
+  plane(min(K0, gc.nz - 1), pv);
+#pragma unroll
+  for (int t = 0; t < kPc; ++t) {
+    const int K = K0 + t;
+    if (K >= gc.nz) break;
+    emit(2 * K, pv);
+    if (2 * K + 1 >= gf.nz) break;
+    plane(min(K + 1, gc.nz - 1), cv);
+    A mv[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        mv[r][c] = A(0.5) * (pv[r][c] + cv[r][c]);
+        pv[r][c] = cv[r][c];
+      }
+    emit(2 * K + 1, mv);
   }
 }
+
+// Fine planes per thread of the batched prolongation.
+constexpr int kPz = 8;
 
 // Batched transfers: CTA b handles block (b - first) of instance entry `lo` (a grid of 32 x 4
 // thread blocks over (x, y) times z-blocks).
@@ -268,11 +322,35 @@ __global__ void k_prolong_batch(const BatchXfer* __restrict__ tab, int count, in
 
 template <typename T>
 int restrict_t(const void* rf, const LevelGeom& gf, void* rc, const LevelGeom& gc, cudaStream_t s) {
-  if ((gf.pitch & 1) || (reinterpret_cast<uintptr_t>(rf) % (2 * sizeof(T))))
-    return set_error(NN4_EINVAL, "restriction needs an even row pitch and an aligned fine field");
-  dim3 blk(32, 4);
-  dim3 grd((gc.nx + 31) / 32, (gc.ny + 3) / 4, (gc.nz + kRz - 1) / kRz);
-  k_restrict<T><<<grd, blk, 0, s>>>(static_cast<const T*>(rf), static_cast<T*>(rc), gf, gc);
+  using Lay = RLay<T, kRTy, kRStages>;
+  if (reinterpret_cast<uintptr_t>(rf) % 16 || (gf.pitch * (long long)sizeof(T)) % 16)
+    return set_error(NN4_EINVAL, "restriction needs a 16-byte aligned fine field and row pitch");
+  if (gc.nx < 2 || gc.ny < 1 || gc.nz < 1) return set_error(NN4_EINVAL, "restriction: empty coarse grid");
+  const nn4_dtype dt = sizeof(T) == 8 ? NN4_F64 : (sizeof(T) == 4 ? NN4_F32 : NN4_BF16);
+  CUtensorMap m;
+  if (!make_tmap_3d(&m, dt, rf, gf.nx, gf.ny, gf.nz, gf.pitch, Lay::BX, Lay::BY))
+    return set_error(NN4_ECUDA, "tensor map encoding failed (restriction)");
+  auto kern = k_restrict<T, kRTy, kRStages>;
+  static int per_sm = 0;  // resident CTAs per SM (set once per instantiation)
+  if (!per_sm) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kRTy, Lay::SMEM) != cudaSuccess)
+      return check_cuda(cudaGetLastError(), "restriction occupancy");
+    per_sm = std::max(per_sm, 1);
+  }
+  const int tiles_x = (gc.nx - 1 + 31) / 32, tiles_y = (gc.ny + kRTy - 1) / kRTy;
+  // coarse planes per CTA: the fewest waves of resident CTAs times the fine planes each CTA reads
+  const long long resident = (long long)per_sm * sm_count();
+  int kc = gc.nz;
+  long long best = -1;
+  for (int c : {16, 12, 8, 6, 4, 3, 2, 1}) {
+    const int cc = std::min(c, gc.nz);
+    const long long blocks = (long long)tiles_x * tiles_y * ((gc.nz + cc - 1) / cc);
+    const long long cost = (blocks + resident - 1) / resident * (2 * cc + 1);
+    if (best < 0 || cost < best) best = cost, kc = cc;
+  }
+  dim3 grd(tiles_x, tiles_y, (gc.nz + kc - 1) / kc);
+  kern<<<grd, dim3(32, kRTy), Lay::SMEM, s>>>(m, static_cast<T*>(rc), gc, kc);
   return check_cuda(cudaGetLastError(), "restrict launch");
 }
 
@@ -283,7 +361,7 @@ int prolong_t(const void* ec, const LevelGeom& gc, void* ef, const void* base, c
       (base && reinterpret_cast<uintptr_t>(base) % (2 * sizeof(T))))
     return set_error(NN4_EINVAL, "prolongation needs an even row pitch and aligned fine fields");
   dim3 blk(32, 4);
-  dim3 grd((gc.nx + 31) / 32, (gf.ny + 3) / 4, (gf.nz + kPz - 1) / kPz);
+  dim3 grd((gc.nx + 31) / 32, (gc.ny + 3) / 4, (gc.nz + kPc - 1) / kPc);
   k_prolong<T><<<grd, blk, 0, s>>>(static_cast<const T*>(ec), static_cast<T*>(ef), static_cast<const T*>(base), gc, gf);
   return check_cuda(cudaGetLastError(), "prolong launch");
 }
