@@ -36,10 +36,12 @@ __device__ __forceinline__ void st2(bf16* p, float a, float b) {
 // exist; zero at coarse Dirichlet nodes.  A CTA owns 32 coarse columns x TYC coarse rows and marches
 // along z over `kchunk` coarse planes: every fine plane 2K-1 .. 2K+1 of its region (fine columns
 // 2 I0 - 1 .. 2 I0 + 63, rows 2 J0 - 1 .. 2 J0 + 2 TYC - 1) arrives as one TMA box in a ring of S
-// stages, each fine value leaves HBM once per chunk, and fine nodes outside the grid arrive as
-// zeros (their weight).  A thread restricts its coarse node in x and y from the box and folds the
-// z weights (1/2, 1, 1/2) into one running sum.  Rows of 32 m + 1 coarse nodes: the last tile's first
-// lane also computes coarse column 32 m.
+// stages (a power of two), each fine value leaves HBM once per chunk, and fine nodes outside the
+// grid arrive as zeros (their weight).  A thread owns one coarse column and RPT consecutive coarse
+// rows: it restricts the 2 RPT + 1 fine rows of a plane in x once (the fine pair as one load, the
+// left neighbour from the previous lane), combines them in y per coarse row, and folds the z
+// weights (1/2, 1, 1/2) into one running sum per coarse node.  Rows of 32 m + 1 coarse nodes: the
+// last tile's first lane also computes coarse column 32 m.
 template <typename T, int TYC, int S>
 struct RLay {
   static constexpr int AL = 16 / (int)sizeof(T);
@@ -48,15 +50,16 @@ struct RLay {
   static constexpr int BYTES = BX * BY * (int)sizeof(T);
   static constexpr int STAGE = (BYTES + 127) / 128 * 128;
   static constexpr size_t SMEM = (size_t)S * STAGE + S * 8;
+  static_assert((S & (S - 1)) == 0, "ring depth is a power of two");
 };
-constexpr int kRTy = 8, kRStages = 6;
+constexpr int kRTy = 8, kRpt = 2, kRStages = 8;
 
-template <typename T, int TYC, int S>
-__global__ void __launch_bounds__(32 * TYC) k_restrict(const __grid_constant__ CUtensorMap fmap, T* __restrict__ rc,
-                                                       const LevelGeom gc, int kchunk) {
+template <typename T, int TYC, int RPT, int S>
+__global__ void __launch_bounds__(32 * TYC / RPT) k_restrict(const __grid_constant__ CUtensorMap fmap,
+                                                             T* __restrict__ rc, const LevelGeom gc, int kchunk) {
   using A = typename Acc<T>::type;
   using Lay = RLay<T, TYC, S>;
-  constexpr int AL = Lay::AL, BX = Lay::BX;
+  constexpr int AL = Lay::AL, BX = Lay::BX, NR = 2 * RPT + 1;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * Lay::STAGE);
   const int I0 = blockIdx.x * 32, J0 = blockIdx.y * TYC;
@@ -72,44 +75,60 @@ __global__ void __launch_bounds__(32 * TYC) k_restrict(const __grid_constant__ C
   }
   __syncthreads();
   auto issue = [&](int q) {
-    const int s = q % S;
+    const int s = q & (S - 1);
     mbar_expect_tx(&bars[s], Lay::BYTES);
     tma_load_3d(smem + s * Lay::STAGE, &fmap, 2 * I0 - AL, 2 * J0 - 1, f0 + q, &bars[s]);
   };
   int issued = min(S, nf);
   if (tid == 0)
     for (int q = 0; q < issued; ++q) issue(q);
-  const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+  const int I = I0 + threadIdx.x, Jb = J0 + RPT * threadIdx.y;
   const bool extra = threadIdx.x == 0 && I0 + 32 == gc.nx - 1;
-  const int cb = (2 * threadIdx.y + 1) * BX + 2 * threadIdx.x + AL;  // fine node (2I, 2J) in a box
-  const bool dxy = (gc.dir[2] && J == 0) || (gc.dir[3] && J == gc.ny - 1);
+  const int cb = 2 * RPT * threadIdx.y * BX + 2 * threadIdx.x + AL;  // fine node (2I, 2Jb - 1) in a box
   const bool dx = (gc.dir[0] && I == 0) || (gc.dir[1] && I == gc.nx - 1);
   const bool dx2 = gc.dir[1];  // the extra column is the last one
   const long long cps = gc.pitch * (long long)gc.ny;
-  T* const out = rc + I + gc.pitch * (long long)J;
-  A acc = A(0), acc2 = A(0);
+  T* const out = rc + I + gc.pitch * (long long)Jb;
+  A acc[RPT], acc2[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) acc[r] = acc2[r] = A(0);
   bool failed = false;
   int q = 0;
   for (; q < nf; ++q) {
-    const int s = q % S;
+    const int s = q & (S - 1);
     if (!mbar_wait_bounded(&bars[s], (uint32_t)((q / S) & 1))) failed = true;
     const T* F = reinterpret_cast<const T*>(smem + s * Lay::STAGE);
-    auto row = [&](int c) { return to_acc(F[c]) + A(0.5) * (to_acc(F[c - 1]) + to_acc(F[c + 1])); };
-    auto xy = [&](int c) { return row(c) + A(0.5) * (row(c - BX) + row(c + BX)); };
-    const A v = xy(cb);
-    const A v2 = extra ? xy(cb + 64) : A(0);
-    if ((f0 + q) & 1) {  // odd fine plane: closes coarse plane (f-1)/2, opens (f+1)/2
-      if (q > 0 && !failed && J < gc.ny) {
-        const int K = (f0 + q - 1) >> 1;
-        const bool dz = dxy || (gc.dir[4] && K == 0) || (gc.dir[5] && K == gc.nz - 1);
-        if (I < gc.nx) out[cps * K] = from_acc<T>((dz || dx) ? A(0) : acc + A(0.5) * v);
-        if (extra) out[cps * K + 32] = from_acc<T>((dz || dx2) ? A(0) : acc2 + A(0.5) * v2);
+    A xr[NR], xr2[NR];  // the fine rows restricted in x
+#pragma unroll
+    for (int w = 0; w < NR; ++w) {
+      const int c = cb + w * BX;
+      A a, b;
+      ld2(F + c, a, b);
+      A l = __shfl_up_sync(0xffffffffu, b, 1);
+      if (threadIdx.x == 0) l = to_acc(F[c - 1]);
+      xr[w] = a + A(0.5) * (l + b);
+      xr2[w] = extra ? to_acc(F[c + 64]) + A(0.5) * (to_acc(F[c + 63]) + to_acc(F[c + 65])) : A(0);
+    }
+    const bool odd = (f0 + q) & 1;  // odd fine plane: closes coarse plane (f-1)/2, opens (f+1)/2
+    const int K = (f0 + q - 1) >> 1;
+    const bool dz = (gc.dir[4] && K == 0) || (gc.dir[5] && K == gc.nz - 1);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const A v = xr[2 * r + 1] + A(0.5) * (xr[2 * r] + xr[2 * r + 2]);
+      const A v2 = xr2[2 * r + 1] + A(0.5) * (xr2[2 * r] + xr2[2 * r + 2]);
+      if (odd) {
+        const int J = Jb + r;
+        if (q > 0 && !failed && J < gc.ny) {
+          const bool dn = dz || (gc.dir[2] && J == 0) || (gc.dir[3] && J == gc.ny - 1);
+          if (I < gc.nx) out[cps * K + gc.pitch * r] = from_acc<T>((dn || dx) ? A(0) : acc[r] + A(0.5) * v);
+          if (extra) out[cps * K + gc.pitch * r + 32] = from_acc<T>((dn || dx2) ? A(0) : acc2[r] + A(0.5) * v2);
+        }
+        acc[r] = A(0.5) * v;
+        acc2[r] = A(0.5) * v2;
+      } else {
+        acc[r] += v;
+        acc2[r] += v2;
       }
-      acc = A(0.5) * v;
-      acc2 = A(0.5) * v2;
-    } else {
-      acc += v;
-      acc2 += v2;
     }
     if (__syncthreads_or(failed)) {
       failed = true;
@@ -121,97 +140,151 @@ __global__ void __launch_bounds__(32 * TYC) k_restrict(const __grid_constant__ C
     }
   }
   if (failed && tid == 0) {
-    for (int p = q; p < issued; ++p) mbar_wait_bounded(&bars[p % S], (uint32_t)((p / S) & 1));
+    for (int p = q; p < issued; ++p) mbar_wait_bounded(&bars[p & (S - 1)], (uint32_t)((p / S) & 1));
   }
 }
 
 // Prolongation e_f (+)= P e_c: each fine node takes the coarse nodes bracketing it, weight 1 at an
 // even index and 1/2 for each of the two parents at an odd index, per axis, applied in the order
-// y, then x, then z.  A thread owns coarse column I and coarse row J: the fine pair (2I, 2I+1) of
-// fine rows 2J and 2J+1, over the fine planes of kPc coarse planes (2 kPc fine planes).  Per coarse
-// plane it loads two values (rows J and J+1 of column I) and takes column I+1 from the next lane,
-// forms the four plane values (row parity x column parity) and stores one fine pair per fine row
-// and plane; odd fine planes average two consecutive plane values.  Dirichlet fine nodes keep base
-// (or 0).
+// y, then x, then z.  A thread owns coarse columns I = 2L, 2L+1 and coarse row J: the fine columns
+// 4L .. 4L+3 of fine rows 2J and 2J+1, over the fine planes of kPc coarse planes (2 kPc fine
+// planes).  It loads the coarse values of columns 2L .. 2L+2, rows J and J+1, of its kPc + 1 coarse
+// planes first, forms the plane values (row parity x 4 columns) per coarse plane and stores four
+// fine values per fine row and plane as one vector; odd fine planes average two consecutive plane
+// values.  For rows of 4 m + 1 fine nodes whose last lane ends at column 4 m - 1, that lane also
+// stores fine column 4 m.  Dirichlet fine nodes keep base (or 0).
 constexpr int kPc = 4;
 
-template <typename T>
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  static __device__ __forceinline__ void st(float* p, const float v[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  static __device__ __forceinline__ void ld(const float* p, float v[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  }
+};
+template <> struct Vec4<double> {
+  static __device__ __forceinline__ void st(double* p, const double v[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+  static __device__ __forceinline__ void ld(const double* p, double v[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+};
+template <> struct Vec4<bf16> {
+  static __device__ __forceinline__ void st(bf16* p, const float v[4]) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned*>(&a);
+    u.y = *reinterpret_cast<unsigned*>(&b);
+    *reinterpret_cast<uint2*>(p) = u;
+  }
+  static __device__ __forceinline__ void ld(const bf16* p, float v[4]) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+  }
+};
+
+template <typename T, bool BASE>
 __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ ec, T* ef, const T* base, const LevelGeom gc,
-                                                 const LevelGeom gf) {
+                                                 const LevelGeom gf, int lanes_x) {
   using A = typename Acc<T>::type;
-  const int lane = threadIdx.x;
-  const int I = blockIdx.x * 32 + lane;
+  const int L = blockIdx.x * 32 + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (J >= gc.ny) return;  // whole warps only (J is uniform across the warp)
-  const int Ic = min(I, gc.nx - 1);
+  const int Ia = min(2 * L, gc.nx - 1), Ib = min(2 * L + 1, gc.nx - 1), In = min(2 * L + 2, gc.nx - 1);
   const int Jn = min(J + 1, gc.ny - 1);  // row J+1 (clamped: its values then feed no stored node)
   const long long cps = gc.pitch * (long long)gc.ny;
-  const T* const r0 = ec + Ic + gc.pitch * (long long)J;
+  const T* const r0 = ec + gc.pitch * (long long)J;
   const long long d1 = gc.pitch * (long long)(Jn - J);
   const int K0 = blockIdx.z * kPc;
-  const int i = 2 * I, j = 2 * J;
-  const bool ok0 = I < gc.nx, ok1 = i + 1 < gf.nx;  // fine columns 2I and 2I+1 exist
-  const bool okr = j + 1 < gf.ny;                    // fine row 2J+1 exists
-  const bool dx0 = (gf.dir[0] && i == 0) || (gf.dir[1] && i == gf.nx - 1);
-  const bool dx1 = gf.dir[1] && i + 1 == gf.nx - 1;
-  const bool dy0 = (gf.dir[2] && j == 0) || (gf.dir[3] && j == gf.ny - 1);
-  const bool dy1 = gf.dir[3] && j + 1 == gf.ny - 1;
-  const long long fps = gf.pitch * (long long)gf.ny;
-  T* const out0 = ef + i + gf.pitch * (long long)j;
-  // plane values of coarse plane K: [row parity][column parity]
-  auto plane = [&](int K, A v[2][2]) {
-    const T* p = r0 + cps * K;
-    const A c0 = to_acc(p[0]), c1 = to_acc(p[d1]);
-    A n0 = __shfl_down_sync(0xffffffffu, c0, 1), n1 = __shfl_down_sync(0xffffffffu, c1, 1);
-    if (lane == 31 || Ic + 1 >= gc.nx) {  // column I+1 from memory (clamped at the last column)
-      const int o = Ic + 1 < gc.nx ? 1 : 0;
-      n0 = to_acc(p[o]);
-      n1 = to_acc(p[d1 + o]);
+  // raw values of coarse planes K0 .. K0 + kPc (clamped into the grid), rows J, J+1, columns
+  // Ia, Ib, In: every load first
+  A ca[kPc + 1][2], cb[kPc + 1][2], cn[kPc + 1][2];
+#pragma unroll
+  for (int t = 0; t <= kPc; ++t) {
+    const T* p = r0 + cps * min(K0 + t, gc.nz - 1);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const T* pr = p + (r ? d1 : 0);
+      ca[t][r] = to_acc(pr[Ia]);
+      cb[t][r] = to_acc(pr[Ib]);
+      cn[t][r] = to_acc(pr[In]);
     }
-    v[0][0] = c0;                     // even row, even column
-    v[0][1] = A(0.5) * (c0 + n0);     // even row, odd column
-    const A a = A(0.5) * (c0 + c1);   // odd row: y first
-    const A an = A(0.5) * (n0 + n1);
-    v[1][0] = a;
-    v[1][1] = A(0.5) * (a + an);
+  }
+  const int f = 4 * L, j = 2 * J;
+  const bool full = f + 3 < gf.nx;                                // all four fine columns exist
+  const bool extra = f + 4 == gf.nx - 1 && L + 1 == lanes_x;       // also the last fine column
+  const bool okr = j + 1 < gf.ny;                                  // fine row 2J+1 exists
+  bool dxe[5];                                                     // Dirichlet fine columns
+#pragma unroll
+  for (int e = 0; e < 5; ++e) dxe[e] = (gf.dir[0] && f + e == 0) || (gf.dir[1] && f + e == gf.nx - 1);
+  const bool dy[2] = {(gf.dir[2] && j == 0) || (gf.dir[3] && j == gf.ny - 1), gf.dir[3] && j + 1 == gf.ny - 1};
+  const long long fps = gf.pitch * (long long)gf.ny;
+  T* const out0 = ef + f + gf.pitch * (long long)j;
+  // plane values of coarse plane K0 + t at fine columns f .. f+4: y first, then x
+  auto plane = [&](int t, A v[2][5]) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const A a = r ? A(0.5) * (ca[t][0] + ca[t][1]) : ca[t][0];
+      const A b = r ? A(0.5) * (cb[t][0] + cb[t][1]) : cb[t][0];
+      const A n = r ? A(0.5) * (cn[t][0] + cn[t][1]) : cn[t][0];
+      v[r][0] = a;
+      v[r][1] = A(0.5) * (a + b);
+      v[r][2] = b;
+      v[r][3] = A(0.5) * (b + n);
+      v[r][4] = n;
+    }
   };
-  // one fine plane k from plane values v: Dirichlet nodes keep base (or 0)
-  auto emit = [&](int k, const A v[2][2]) {
-    if (k >= gf.nz) return;
+  auto emit = [&](int k, const A v[2][5]) {
     const bool dz = (gf.dir[4] && k == 0) || (gf.dir[5] && k == gf.nz - 1);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (r == 1 && !okr) break;
-      T* out = out0 + fps * k + gf.pitch * r;
-      const bool dyr = dz || (r ? dy1 : dy0);
-      A b0 = A(0), b1 = A(0);
-      if (base) {
-        const T* bp = base + (out - ef);
-        if (ok1) ld2(bp, b0, b1);
-        else if (ok0) b0 = to_acc(bp[0]);
+      T* out = out0 + fps * k + (r ? gf.pitch : 0);
+      A bv[4] = {A(0), A(0), A(0), A(0)};
+      if (BASE && full) Vec4<T>::ld(base + (out - ef), bv);
+      A w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (BASE && !full && f + e < gf.nx) bv[e] = to_acc(base[(out - ef) + e]);
+        w[e] = (dz || dy[r] || dxe[e]) ? bv[e] : v[r][e] + bv[e];
       }
-      const A v0 = (dyr || dx0) ? b0 : v[r][0] + b0;
-      const A v1 = (dyr || dx1) ? b1 : v[r][1] + b1;
-      if (ok1) st2(out, v0, v1);
-      else if (ok0) out[0] = from_acc<T>(v0);
+      if (full) {
+        Vec4<T>::st(out, w);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (f + e < gf.nx) out[e] = from_acc<T>(w[e]);
+      }
+      if (extra) {
+        const A b4 = BASE ? to_acc(base[(out - ef) + 4]) : A(0);
+        out[4] = from_acc<T>((dz || dy[r] || dxe[4]) ? b4 : v[r][4] + b4);
+      }
     }
   };
-  A pv[2][2], cv[2][2];
-  plane(min(K0, gc.nz - 1), pv);
+  A pv[2][5], cv[2][5];
+  plane(0, pv);
 #pragma unroll
   for (int t = 0; t < kPc; ++t) {
     const int K = K0 + t;
     if (K >= gc.nz) break;
     emit(2 * K, pv);
     if (2 * K + 1 >= gf.nz) break;
-    plane(min(K + 1, gc.nz - 1), cv);
-    A mv[2][2];
+    plane(t + 1, cv);
+    A mv[2][5];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        mv[r][c] = A(0.5) * (pv[r][c] + cv[r][c]);
-        pv[r][c] = cv[r][c];
+      for (int e = 0; e < 5; ++e) {
+        mv[r][e] = A(0.5) * (pv[r][e] + cv[r][e]);
+        pv[r][e] = cv[r][e];
       }
     emit(2 * K + 1, mv);
   }
@@ -330,11 +403,11 @@ int restrict_t(const void* rf, const LevelGeom& gf, void* rc, const LevelGeom& g
   CUtensorMap m;
   if (!make_tmap_3d(&m, dt, rf, gf.nx, gf.ny, gf.nz, gf.pitch, Lay::BX, Lay::BY))
     return set_error(NN4_ECUDA, "tensor map encoding failed (restriction)");
-  auto kern = k_restrict<T, kRTy, kRStages>;
+  auto kern = k_restrict<T, kRTy, kRpt, kRStages>;
   static int per_sm = 0;  // resident CTAs per SM (set once per instantiation)
   if (!per_sm) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Lay::SMEM) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kRTy, Lay::SMEM) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kRTy / kRpt, Lay::SMEM) != cudaSuccess)
       return check_cuda(cudaGetLastError(), "restriction occupancy");
     per_sm = std::max(per_sm, 1);
   }
@@ -350,19 +423,30 @@ int restrict_t(const void* rf, const LevelGeom& gf, void* rc, const LevelGeom& g
     if (best < 0 || cost < best) best = cost, kc = cc;
   }
   dim3 grd(tiles_x, tiles_y, (gc.nz + kc - 1) / kc);
-  kern<<<grd, dim3(32, kRTy), Lay::SMEM, s>>>(m, static_cast<T*>(rc), gc, kc);
+  kern<<<grd, dim3(32, kRTy / kRpt), Lay::SMEM, s>>>(m, static_cast<T*>(rc), gc, kc);
   return check_cuda(cudaGetLastError(), "restrict launch");
 }
 
 template <typename T>
 int prolong_t(const void* ec, const LevelGeom& gc, void* ef, const void* base, const LevelGeom& gf,
               cudaStream_t s) {
-  if ((gf.pitch & 1) || (reinterpret_cast<uintptr_t>(ef) % (2 * sizeof(T))) ||
-      (base && reinterpret_cast<uintptr_t>(base) % (2 * sizeof(T))))
-    return set_error(NN4_EINVAL, "prolongation needs an even row pitch and aligned fine fields");
+  // one vector access of four fine values: 16 bytes (8 for BF16); rows of a multiple of 16 bytes
+  const size_t vb = std::min<size_t>(16, 4 * sizeof(T));
+  if ((gf.pitch * (long long)sizeof(T)) % 16 || (reinterpret_cast<uintptr_t>(ef) % vb) ||
+      (base && reinterpret_cast<uintptr_t>(base) % vb))
+    return set_error(NN4_EINVAL, "prolongation needs 16-byte rows and aligned fine fields");
+  // lanes of four fine columns: cover columns 0 .. 64 m - 1 of a 64 m + 1 row (the last lane also
+  // takes the last column), else every column
+  const int lanes = std::max(1, (gf.nx - 1 + 3) / 4);
+  const int tiles_x = (lanes + 31) / 32;
   dim3 blk(32, 4);
-  dim3 grd((gc.nx + 31) / 32, (gc.ny + 3) / 4, (gc.nz + kPc - 1) / kPc);
-  k_prolong<T><<<grd, blk, 0, s>>>(static_cast<const T*>(ec), static_cast<T*>(ef), static_cast<const T*>(base), gc, gf);
+  dim3 grd(tiles_x, (gc.ny + 3) / 4, (gc.nz + kPc - 1) / kPc);
+  const int lanes_x = 32 * tiles_x;
+  if (base)
+    k_prolong<T, true><<<grd, blk, 0, s>>>(static_cast<const T*>(ec), static_cast<T*>(ef), static_cast<const T*>(base),
+                                          gc, gf, lanes_x);
+  else
+    k_prolong<T, false><<<grd, blk, 0, s>>>(static_cast<const T*>(ec), static_cast<T*>(ef), nullptr, gc, gf, lanes_x);
   return check_cuda(cudaGetLastError(), "prolong launch");
 }
 
