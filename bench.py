@@ -858,7 +858,10 @@ def bytes_per_node(name, s):
         "inner:direction": s + 8.0,    # z read (storage type), FP32 p_old read, FP32 p written
         "restrict:L0": 1.125 * s,      # per fine node: fine read, 1/8 coarse written
         "prolong:L0": 1.125 * s,       # per fine node: fine written, 1/8 coarse read
-        "pass27:jacobi:L1": 30.0 * s,  # per level-1 node: 27 Galerkin coefficients, x (haloed), b read, e written
+        # per level-1 node: the 14 stored coefficients of the symmetric Galerkin operator (the centre
+        # and the 13 after it; the other 13 are the neighbours' mirrored entries), x (haloed), b read,
+        # e written
+        "pass27:jacobi:L1": 17.0 * s,
         "residual_restrict:L0": 3.125 * s,  # per fine node: x (haloed), k, b read; 1/8 coarse written
     }
     return table.get(name)
