@@ -193,7 +193,10 @@ struct GridBarrier {
   unsigned count;
   unsigned gen;
 };
-constexpr int kCoarseThreads = 512;
+// Threads per block of the cooperative coarse-level launch: blocks of 256 spread the 33^3 level of a
+// 257^3 hierarchy over 141 SMs (measured 32.8 us per cycle's coarse levels, against 40.2 us with 512
+// and 34.9 us with 128).
+constexpr int kCoarseThreads = 256;
 constexpr long long kCoarseNodes = 40000;
 int launch_coarse(nn4_dtype dt, const TailArgs& a, GridBarrier* bar, cudaStream_t s);
 // One CTA per instance (tab: device array of `count` tails; `active` skips converged ones).
