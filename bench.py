@@ -193,8 +193,8 @@ def ncu_names(tn):
         (r"k_pass<double, 3,", "pass64:matvec"), (r"k_pass<double, 1,", "pass64:residual"),
         (f"k_pass<{tn}, 2, 2,", "pass:jacobi:L0"), (r"k_pass<float, 3,", "inner:matvec"),
         (f"k_fcg_update<float, {tn}>", "inner:update"), (f"k_new_direction<{tn}, float>", "inner:direction"),
-        (f"k_restrict<{tn}>", "restrict:L0"), (f"k_prolong<{tn}>", "prolong:L0"),
-        (f"k_pass27<{tn}, 2>", "pass27:jacobi:L1"), (f"k_coarse<{tn}>", "coarse_levels"),
+        (f"k_restrict<{tn},", "restrict:L0"), (f"k_prolong<{tn},", "prolong:L0"),
+        (f"k_pass27<{tn}, 2,", "pass27:jacobi:L1"), (f"k_coarse<{tn}>", "coarse_levels"),
     ]
 
 
@@ -880,7 +880,7 @@ _PASS = ("stencil.cu", "pass_tile.cuh")
 KERNEL_SOURCE = {"pass64:matvec": _PASS, "pass64:residual": _PASS, "pass:jacobi:L0": _PASS,
                  "inner:matvec": _PASS, "inner:update": ("outer.cu",), "inner:direction": ("outer.cu",),
                  "inner:dot": ("outer.cu",), "restrict:L0": ("transfer.cu",), "prolong:L0": ("transfer.cu",),
-                 "pass27:jacobi:L1": ("galerkin.cu",), "coarse_levels": ("tail.cu",),
+                 "pass27:jacobi:L1": ("galerkin.cu",), "coarse_levels": ("tail.cu", "internal.h"),
                  "residual_restrict:L0": ("resrestrict.cu", "pass_tile.cuh")}
 
 
