@@ -67,9 +67,15 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi takes a moment to start: let its first sample arrive before the timed
+            # region begins, so that the samples cover the region
+            t0 = time.perf_counter()
+            while not self.samples and self.proc.poll() is None and time.perf_counter() - t0 < 3.0:
+                time.sleep(0.01)
+            self.samples.clear()
         except OSError:
             self.proc = None
         return self
