@@ -394,6 +394,10 @@ int launch_convert(nn4_dtype ta, const void* a, const LevelGeom& ga, nn4_dtype t
       NN4_CHECK_CHUNKS(ga);
       k_convert<float, bf16><<<cw_grid(k_convert<float, bf16>, ga), kCwBlock, 0, s>>>(static_cast<const float*>(a), ga, static_cast<bf16*>(b), gb);
       break;
+    case NN4_F64 * 3 + NN4_F64:  // a copy between two pitches (dense host layout <-> plan layout)
+      NN4_CHECK_CHUNKS(ga);
+      k_convert<double, double><<<cw_grid(k_convert<double, double>, ga), kCwBlock, 0, s>>>(static_cast<const double*>(a), ga, static_cast<double*>(b), gb);
+      break;
     case NN4_F32 * 3 + NN4_F64:
       NN4_CHECK_CHUNKS(ga);
       k_convert<float, double><<<cw_grid(k_convert<float, double>, ga), kCwBlock, 0, s>>>(static_cast<const float*>(a), ga, static_cast<double*>(b), gb);

@@ -1452,18 +1452,30 @@ int nn4_pressure_solve_host(nn4_plan p, const double* b_host, double* x_host, do
   PlanImpl* P = p->impl;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const LevelGeom& g = P->g64;
-  const size_t w = (size_t)g.nx * sizeof(double);
-  const size_t dp = (size_t)g.pitch * sizeof(double);
+  const size_t dense = (size_t)g.nx * g.ny * g.nz * sizeof(double);
   int rc;
-  if ((rc = check_cuda(cudaMemcpy2DAsync(P->b64, dp, b_host, w, w, (size_t)g.ny * g.nz, cudaMemcpyHostToDevice, s),
-                       "copy b in")) ||
-      (rc = check_cuda(cudaMemcpy2DAsync(P->x64, dp, x_host, w, w, (size_t)g.ny * g.nz, cudaMemcpyHostToDevice, s),
-                       "copy x in")))
-    return rc;
+  // The host arrays are dense (row pitch nx).  Each goes over the link as one contiguous copy into
+  // the FP64 residual field (free until the solve writes its first residual; as large as a pitched
+  // field), and a device kernel moves it to the plan's row pitch: a pitched copy of rows of a few
+  // kilobytes runs the host link far below its rate.
+  LevelGeom gd = g;
+  gd.pitch = g.nx;
+  const bool same = g.pitch == g.nx;
+  auto in = [&](const double* h, double* d, const char* what) {
+    int r;
+    if (same) return check_cuda(cudaMemcpyAsync(d, h, dense, cudaMemcpyHostToDevice, s), what);
+    if ((r = check_cuda(cudaMemcpyAsync(P->r64, h, dense, cudaMemcpyHostToDevice, s), what))) return r;
+    return launch_convert(NN4_F64, P->r64, gd, NN4_F64, d, g, s);
+  };
+  if ((rc = in(b_host, P->b64, "copy b in")) || (rc = in(x_host, P->x64, "copy x in"))) return rc;
   const int st = solve_device(P, rtol, max_iters, info, s);
   if (st != NN4_OK && st != NN4_ENOCONV) return st;
-  if ((rc = check_cuda(cudaMemcpy2DAsync(x_host, w, P->x64, dp, w, (size_t)g.ny * g.nz, cudaMemcpyDeviceToHost, s),
-                       "copy x out")) ||
+  const double* xs = P->x64;
+  if (!same) {
+    if ((rc = launch_convert(NN4_F64, P->x64, g, NN4_F64, P->r64, gd, s))) return rc;
+    xs = P->r64;
+  }
+  if ((rc = check_cuda(cudaMemcpyAsync(x_host, xs, dense, cudaMemcpyDeviceToHost, s), "copy x out")) ||
       (rc = check_cuda(cudaStreamSynchronize(s), "sync")))
     return rc;
   return st;
