@@ -146,6 +146,7 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
   constexpr int BXC = Lay::BXC, CT_BYTES = Lay::CT_BYTES, CT_PAD = Lay::CT_PAD, CT_OFF = Lay::CT_OFF;
   constexpr int STAGE = Lay::STAGE;
   constexpr bool HAS_B = Lay::HAS_B, RR = Lay::RR;
+  constexpr bool KX_PLANE = VC == 2 && sizeof(T) == 8;  // k x formed once per plane (FP64 passes)
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * STAGE);
   double* red = reinterpret_cast<double*>(bars + S);
@@ -302,11 +303,24 @@ __device__ __forceinline__ bool pass_tile(const Maps* mp, const PassArgs& a, int
     A ux[RY], vx[RY], xcn[RY];
     plane_uv<T, A, RY, false, ISO>(tx_, tx_, rowoff, cc, cl, cr, c, sx.p2, ux, vx, xcn);
     A ukx[RY], vkx[RY], uk[RY], vk[RY], kcn[RY];
-    if (VC) plane_uv<T, A, RY, true, ISO>(tx_, tk_, rowoff, cc, cl, cr, c, skx.p2, ukx, vkx, nullptr);
-    if (VC == 1) plane_uv<T, A, RY, false, ISO>(tk_, tk_, rowoff, cc, cl, cr, c, sk.p2, uk, vk, kcn);
-    if (VC == 2) {
+    if constexpr (KX_PLANE) {
+      // FP64 with (1/2) L k stored: every k x product of the haloed plane is formed once (instead
+      // of once per thread that reads it, about three times) into the k tile, which holds nothing
+      // else this plane needs once each thread has its centre values of k
 #pragma unroll
       for (int r = 0; r < RY; ++r) kcn[r] = to_acc(tk_[rowoff[r + 1] + cc]);
+      __syncthreads();
+      T* const kx_ = const_cast<T*>(tk_);
+      for (int e = tid; e < BX * BY; e += TX * TYT) kx_[e] = tx_[e] * kx_[e];
+      __syncthreads();
+      plane_uv<T, A, RY, false, ISO>(tk_, tk_, rowoff, cc, cl, cr, c, skx.p2, ukx, vkx, nullptr);
+    } else {
+      if (VC) plane_uv<T, A, RY, true, ISO>(tx_, tk_, rowoff, cc, cl, cr, c, skx.p2, ukx, vkx, nullptr);
+      if (VC == 1) plane_uv<T, A, RY, false, ISO>(tk_, tk_, rowoff, cc, cl, cr, c, sk.p2, uk, vk, kcn);
+      if (VC == 2) {
+#pragma unroll
+        for (int r = 0; r < RY; ++r) kcn[r] = to_acc(tk_[rowoff[r + 1] + cc]);
+      }
     }
 
     const int kout = zs + q - 2;  // output plane completed by this input plane
