@@ -307,6 +307,18 @@ __global__ void k_convert(const TS* __restrict__ a, LevelGeom ga, TD* __restrict
   }
 }
 
+// The per-iteration device scalars in one launch: p[a], p[b], p[c], p[d] = 0 (negative indices
+// skipped), then p[dst] = p[src] when dst >= 0.  One small kernel instead of separate memset and
+// copy nodes in the captured iterations, each of which costs a few microseconds of the graph.
+__global__ void k_scalars(double* p, int a, int b, int c, int d, int dst, int src) {
+  if (threadIdx.x != 0) return;
+  if (a >= 0) p[a] = 0.0;
+  if (b >= 0) p[b] = 0.0;
+  if (c >= 0) p[c] = 0.0;
+  if (d >= 0) p[d] = 0.0;
+  if (dst >= 0) p[dst] = p[src];
+}
+
 }  // namespace
 
 #define NN4_DISPATCH(dt, call)                         \
@@ -331,6 +343,10 @@ int launch_inv_diag(const double* k, const double* lk, double* invd, const Level
   return check_cuda(cudaGetLastError(), "inverse diagonal");
 }
 
+int launch_scalars(double* p, int a, int b, int c, int d, int dst, int src, cudaStream_t s) {
+  k_scalars<<<1, 32, 0, s>>>(p, a, b, c, d, dst, src);
+  return check_cuda(cudaGetLastError(), "device scalars");
+}
 int launch_masked_copy(const double* b, double* r, const LevelGeom& g, cudaStream_t s) {
   k_masked_copy<<<pw_grid(g), kPwBlock, 0, s>>>(b, r, g);
   return check_cuda(cudaGetLastError(), "masked copy");

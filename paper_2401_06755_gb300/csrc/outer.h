@@ -14,6 +14,9 @@ int launch_to_inner(nn4_dtype dt, const double* r, const LevelGeom& g64, void* r
 // invd = 1 / diag(A) for Eq. k-T from k and lk = (1/2) L k (FP64)
 int launch_inv_diag(const double* k, const double* lk, double* invd, const LevelGeom& g, double c0,
                     cudaStream_t s);
+// Device scalars: p[a], p[b], p[c], p[d] = 0 (negative indices skipped), then p[dst] = p[src] if
+// dst >= 0; one launch
+int launch_scalars(double* p, int a, int b, int c, int d, int dst, int src, cudaStream_t s);
 // r = b at free nodes, 0 at Dirichlet nodes
 int launch_masked_copy(const double* b, double* r, const LevelGeom& g, cudaStream_t s);
 // out += sum of v^2 over all nodes

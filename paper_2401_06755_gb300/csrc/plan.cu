@@ -690,7 +690,7 @@ int inner_krylov(PlanImpl* P, cudaStream_t s) {
   if ((rc = check_cuda(cudaMemsetAsync(P->yi, 0, fb, s), "zero y")) ||
       (rc = check_cuda(cudaMemsetAsync(P->pi[1], 0, fb, s), "zero p")) ||
       (rc = check_cuda(cudaMemsetAsync(P->qi[1], 0, fb, s), "zero q")) ||
-      (rc = check_cuda(cudaMemcpyAsync(P->scal + 10, P->scal + 15, sizeof(double), cudaMemcpyDeviceToDevice, s), "pq")))
+      (rc = K(P, "pointwise:scalars", s, [&] { return launch_scalars(P->scal, -1, -1, -1, -1, 10, 15, s); })))
     return rc;
   if (P->T == NN4_BF16 &&
       (rc = K(P, "pointwise:convert", s, [&] { return launch_convert(NN4_F32, P->ri, P->g32, NN4_BF16, L0.r, L0.g, s); })))
@@ -698,7 +698,9 @@ int inner_krylov(PlanImpl* P, cudaStream_t s) {
   const bool fuse = fused_dot(P);
   for (int j = 0; j < P->o.inner_krylov; ++j) {
     const int par = j & 1, old = 1 - par;
-    if ((rc = check_cuda(cudaMemsetAsync(P->scal + 8, 0, sizeof(double), s), "zero zq"))) return rc;
+    // z.q_old, p.q, p.r of this iteration and |r|^2 of its update start at zero (one launch)
+    if ((rc = K(P, "pointwise:scalars", s, [&] { return launch_scalars(P->scal, 8, 9 + par, 11 + par, 13, -1, 0, s); })))
+      return rc;
     if ((rc = inner_solve(P, s, fuse ? old : -1))) return rc;
     if (!fuse && (rc = K(P, "inner:dot", s, [&] {
                     return launch_dot(P->T, L0.e, L0.g, NN4_F32, P->qi[old], P->g32, P->scal + 8, s);
@@ -708,9 +710,6 @@ int inner_krylov(PlanImpl* P, cudaStream_t s) {
            return launch_direction(P->T, L0.e, L0.g, NN4_F32, P->pi[old], P->pi[par], P->g32, P->scal + 8,
                                    P->scal + 9 + old, s);
          })))
-      return rc;
-    if ((rc = check_cuda(cudaMemsetAsync(P->scal + 9 + par, 0, sizeof(double), s), "zero")) ||
-        (rc = check_cuda(cudaMemsetAsync(P->scal + 11 + par, 0, sizeof(double), s), "zero")))
       return rc;
     PassArgs a{};
     a.g = P->g32;
@@ -726,7 +725,6 @@ int inner_krylov(PlanImpl* P, cudaStream_t s) {
                               &P->m_mat32[par]);
          })))
       return rc;
-    if ((rc = check_cuda(cudaMemsetAsync(P->scal + 13, 0, sizeof(double), s), "zero"))) return rc;
     if ((rc = K(P, "inner:update", s, [&] {
            return launch_update(NN4_F32, P->yi, P->ri, P->pi[par], P->qi[par], P->g32, P->T,
                                 P->T == NN4_BF16 ? L0.r : nullptr, L0.g, P->scal + 11 + par, P->scal + 9 + par,
@@ -768,8 +766,10 @@ int iteration_fcg(PlanImpl* P, int par, cudaStream_t s) {
   const int old = 1 - par;
   int rc;
   ZRef z;
+  // z.q_old, p.q, p.r and |r|^2 of this iteration start at zero (one launch)
+  if ((rc = K(P, "pointwise:scalars", s, [&] { return launch_scalars(P->scal, 2, 3 + par, 5 + par, 0, -1, 0, s); })))
+    return rc;
   if ((rc = precondition(P, s, &z))) return rc;
-  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 2, 0, sizeof(double), s), "zero zq"))) return rc;
   if ((rc = K(P, "pointwise:dot", s,
               [&] { return launch_dot(z.t, z.p, z.g, NN4_F64, P->q64[old], P->g64, P->scal + 2, s); })))
     return rc;
@@ -778,8 +778,6 @@ int iteration_fcg(PlanImpl* P, int par, cudaStream_t s) {
                                  P->scal + 3 + old, s);
        })))
     return rc;
-  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 3 + par, 0, sizeof(double), s), "zero pq"))) return rc;
-  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 5 + par, 0, sizeof(double), s), "zero pr"))) return rc;
   PassArgs a{};
   a.g = P->g64;
   a.L = P->L64;
@@ -794,7 +792,6 @@ int iteration_fcg(PlanImpl* P, int par, cudaStream_t s) {
                             &P->m_mat64[par]);
        })))
     return rc;
-  if ((rc = check_cuda(cudaMemsetAsync(P->scal + 0, 0, sizeof(double), s), "zero norm"))) return rc;
   nn4_dtype tt;
   void* rt;
   LevelGeom gt;
