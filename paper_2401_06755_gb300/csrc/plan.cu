@@ -1083,11 +1083,12 @@ int solve_device(PlanImpl* P, double rtol, int32_t max_iters, nn4_solve_info* in
     residual_sink(P, &tt, &rt, &gt);
     if (rt && (rc = K(P, "pointwise:to_inner", s, [&] { return launch_convert(NN4_F64, P->r64, P->g64, tt, rt, gt, s); })))
       return rc;
+    // the first iteration (parity 0) reads p and q of parity 1 as its old direction and writes
+    // those of parity 0 before reading them: only parity 1 starts at zero
     const size_t fb = field_bytes(P->g64, NN4_F64);
-    for (int t = 0; t < 2; ++t) {
-      if ((rc = check_cuda(cudaMemsetAsync(P->p64[t], 0, fb, s), "zero p"))) return rc;
-      if ((rc = check_cuda(cudaMemsetAsync(P->q64[t], 0, fb, s), "zero q"))) return rc;
-    }
+    if ((rc = check_cuda(cudaMemsetAsync(P->p64[1], 0, fb, s), "zero p")) ||
+        (rc = check_cuda(cudaMemsetAsync(P->q64[1], 0, fb, s), "zero q")))
+      return rc;
     const double one[2] = {1.0, 1.0};
     if ((rc = check_cuda(cudaMemcpyAsync(P->scal + 3, one, sizeof(one), cudaMemcpyHostToDevice, s), "init pq")))
       return rc;
